@@ -1,0 +1,204 @@
+/*
+ * kc.h -- C ABI of libkc, a GB300 (sm_103a) implementation of the hot path of
+ * the exact k-clique counting algorithm FFF_k and its colour-sampling
+ * estimator cFFF_k (Finocchi, Finocchi & Fusco, "Clique counting in
+ * MapReduce: theory and experiments", arXiv:1403.0734).
+ *
+ * The method: order the vertices by (degree, id) (Sec. 2); every k-clique is
+ * counted once, by its smallest vertex u (Sec. 3); u counts the (k-1)-cliques
+ * of G+(u), the subgraph induced by its high-neighbourhood Gamma+(u)
+ * (Algorithm 1, rounds 1-3).  cFFF_k colours every Gamma+(u) independently
+ * with c colours, keeps only monochromatic pairs, and scales the sampled
+ * count by c^(k-2) (Sec. 6, "Color-based sampling").
+ *
+ * Conventions shared by every entry point
+ *   - Graphs are undirected and simple, given as a CSR: off[n+1] (int64,
+ *     off[0] = 0, off[n] = 2m) and adj[2m] (int32); every edge {u,v} appears
+ *     as v in row u and u in row v; rows sorted ascending; no self-loops or
+ *     repeats (the paper's preprocessed input, Sec. 4).  Vertex ids are the
+ *     caller's ids 0..n-1 and break degree ties (Sec. 2).
+ *   - Inputs are owned by the caller and only read.  A kc_graph is owned by
+ *     the library from kc_orient until kc_free.  Outputs are caller-allocated.
+ *   - Pointers are host pointers unless KC_DEVICE_PTRS is set in `flags`, in
+ *     which case the pointer arguments documented as "array" are device
+ *     pointers of the current CUDA device.
+ *   - `stream` is a cudaStream_t (NULL: the legacy default stream).  Calls
+ *     with host outputs return after the result is on the host; calls with
+ *     KC_DEVICE_PTRS outputs are asynchronous on `stream`.
+ *   - Every failure is reported as a kc_status; nothing aborts or traps.
+ *     Kernel-side waits are bounded and report KC_ETIMEOUT.
+ *   - Counts are exact unsigned 64-bit integers; a total that does not fit
+ *     returns KC_EOVERFLOW.
+ */
+#ifndef KC_H
+#define KC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct kc_graph kc_graph;
+
+typedef enum {
+    KC_OK = 0,
+    KC_EINVAL = 1,     /* bad argument, or (with KC_VALIDATE) a malformed CSR */
+    KC_ENOMEM = 2,     /* device or host allocation failed */
+    KC_EOVERFLOW = 3,  /* a count exceeded 2^64 - 1 */
+    KC_ETIMEOUT = 4,   /* a bounded device-side wait gave up */
+    KC_ECUDA = 5,      /* a CUDA runtime call failed (see kc_last_cuda_error) */
+    KC_ENOTSUP = 6     /* request outside the supported range */
+} kc_status;
+
+/* flags */
+#define KC_DEVICE_PTRS 0x1u  /* array arguments are device pointers */
+#define KC_VALIDATE    0x2u  /* kc_orient / kc_count_csr: check the CSR first */
+
+/* Largest k accepted by kc_count / kc_estimate. */
+#define KC_MAX_K 32
+
+/* Human-readable name of a status (static storage). */
+const char* kc_strerror(kc_status s);
+
+/* Text of the last CUDA error seen by this thread (static storage). */
+const char* kc_last_cuda_error(void);
+
+/* Library version, e.g. "kc 0.1 sm_103a". */
+const char* kc_version(void);
+
+/*
+ * kc_build_csr -- preprocessing (Sec. 4: the graphs are made undirected):
+ * turn an arbitrary edge list into the canonical CSR above.  Host-side.
+ *   n        number of vertices; every endpoint must be in [0, n)
+ *   src,dst  ne endpoints (host arrays); either direction, self-loops and
+ *            repeated edges allowed (they are dropped)
+ *   off      out, host array of n+1
+ *   adj      out, host array with room for 2*ne entries
+ *   m_out    out, number of undirected edges kept
+ * Errors: KC_EINVAL (endpoint out of range, n < 0, ne < 0), KC_ENOMEM.
+ */
+kc_status kc_build_csr(int32_t n, const int32_t* src, const int32_t* dst, int64_t ne,
+                       int64_t* off, int32_t* adj, int64_t* m_out);
+
+/*
+ * kc_orient -- Round 1 of Algorithm 1 (Sec. 3, "high-neighborhood
+ * computation") on the device: degrees d(v) (Sec. 2), the total order
+ * x < y iff d(x) < d(y) or (d(x) = d(y) and x < y) (Sec. 2), and every
+ * Gamma+(u) = {x in Gamma(u) : u < x}.  The result is kept resident as an
+ * oriented CSR in rank space (vertex r is the r-th smallest in the order;
+ * row r lists the ranks of Gamma+(r) ascending, i.e. in the order), plus the
+ * work queue used by the counting kernels (owners by |Gamma+| descending).
+ *   off, adj  the canonical CSR (arrays; host or, with KC_DEVICE_PTRS, device)
+ *   n, m      vertices and undirected edges (adj has 2m entries); n >= 0
+ *   flags     KC_DEVICE_PTRS, KC_VALIDATE (symmetry, sorted rows, no loops,
+ *             no repeats; failures return KC_EINVAL)
+ *   out       receives the new graph handle (NULL on failure)
+ * Synchronous: returns when the oriented graph is complete on `stream`.
+ * Errors: KC_EINVAL, KC_ENOMEM, KC_ECUDA.
+ */
+kc_status kc_orient(const int64_t* off, const int32_t* adj, int32_t n, int64_t m,
+                    unsigned flags, void* stream, kc_graph** out);
+
+/* Release a graph and its device memory.  NULL is ignored.  The caller must
+ * ensure no call using `g` is still running on any stream. */
+void kc_free(kc_graph* g);
+
+typedef struct {
+    int32_t n;              /* vertices */
+    int64_t m;              /* undirected edges = sum over u of |Gamma+(u)| */
+    int32_t max_dplus;      /* max |Gamma+(u)|, at most 2 sqrt(m) (App. B, Thm I) */
+    int64_t wedges;         /* sum over u of C(|Gamma+(u)|, 2): Map 2 pairs (App. B, Thm 1) */
+    int64_t device_bytes;   /* device memory held by the handle */
+} kc_graph_info;
+
+/* Statistics of an oriented graph (host struct).  Errors: KC_EINVAL. */
+kc_status kc_info(const kc_graph* g, kc_graph_info* info);
+
+/*
+ * kc_export -- copy the oriented graph out, for checking Round 1.
+ *   rank     array of n: rank[v] = position of vertex v in the order
+ *   perm     array of n: perm[r] = vertex with rank r
+ *   off_plus array of n+1: row offsets of the oriented CSR (rank space)
+ *   adj_plus array of m: ranks of Gamma+ of each row, ascending
+ *   queue    array of n: owners (ranks) by |Gamma+| descending, ties by rank
+ * Any array may be NULL.  Errors: KC_EINVAL, KC_ECUDA.
+ */
+kc_status kc_export(const kc_graph* g, unsigned flags, int32_t* rank, int32_t* perm,
+                    int64_t* off_plus, int32_t* adj_plus, int32_t* queue, void* stream);
+
+/*
+ * kc_count -- FFF_k Rounds 2-3 (Algorithm 1; Sec. 3): for every owner u with
+ * |Gamma+(u)| >= k-1 (the Reduce 1 filter), build G+(u) (the pairs x_i < x_j
+ * of Gamma+(u) that are edges: Map 2 / Reduce 2) and count its (k-1)-cliques
+ * q_{u,k-1} (Reduce 3).  q_k is the sum over u (each clique is counted by its
+ * smallest vertex, Sec. 3).
+ *   k          1..KC_MAX_K; k = 1 gives n and k = 2 gives m (the paper's
+ *              tables list n as q_1 and m as q_2)
+ *   total      out: q_k.  Host pointer; with KC_DEVICE_PTRS a device array of
+ *              two uint64 words (low, high) of the 128-bit sum, high != 0
+ *              meaning the count overflowed
+ *   per_vertex out array of n, nullable: number of k-cliques containing v
+ *              (the per-node counts of Sec. 3, summed over all G+(u));
+ *              their sum is k * q_k
+ *   per_owner  out array of n, nullable: q_{u,k-1}, the Reduce 3 output of
+ *              owner u; their sum is q_k
+ * Both arrays are indexed by the caller's vertex ids.
+ * Errors: KC_EINVAL (k out of range, g NULL), KC_ENOMEM, KC_EOVERFLOW,
+ * KC_ETIMEOUT, KC_ECUDA.
+ */
+kc_status kc_count(const kc_graph* g, int k, unsigned flags, uint64_t* total,
+                   uint64_t* per_vertex, uint64_t* per_owner, void* stream);
+
+/*
+ * kc_estimate -- cFFF_k (Sec. 6, "Color-based sampling"): every owner u colours
+ * each x in Gamma+(u) with colour(u, x) in [0, colours), independently per
+ * owner; Map 2 emits only monochromatic pairs; Reduce 3 counts the
+ * (k-1)-cliques of the sampled G+(u).
+ *   colour(u, x) = floor(h * colours / 2^64) with
+ *   h = mix(seed XOR (0x9E3779B97F4A7C15 * ((uint64)u << 32 | x))), where
+ *   mix is the splitmix64 output function (z ^= z>>30; z *= 0xBF58476D1CE4E5B9;
+ *   z ^= z>>27; z *= 0x94D049BB133111EB; z ^= z>>31), and u, x are the
+ *   caller's vertex ids.
+ *   sampled    out: S = sum of the sampled per-owner counts (exact); with
+ *              KC_DEVICE_PTRS a device array of two uint64 words (low, high)
+ *   estimate   out, host pointer, nullable: S * colours^(k-2) rounded as
+ *              fl(fl(S) * fl(colours^(k-2))) (the Reduce 3 scaling of Sec. 6);
+ *              ignored with KC_DEVICE_PTRS
+ *   per_owner  out array of n, nullable: sampled q_u of every owner
+ *   colours    >= 1; colours = 1 gives exactly kc_count's q_k
+ * Errors: as kc_count.
+ */
+kc_status kc_estimate(const kc_graph* g, int k, uint32_t colours, uint64_t seed,
+                      unsigned flags, uint64_t* sampled, double* estimate,
+                      uint64_t* per_owner, void* stream);
+
+/*
+ * Tuning knobs (process-wide; they change speed, never results).
+ *   KC_PARAM_SMEM_MAX_WORDS  owners whose bitmap rows need at most this many
+ *       32-bit words (|Gamma+(u)| <= 32 * value) keep G+(u) in shared memory;
+ *       wider owners use global-memory tiles.  1..32, default 32.
+ * kc_set_param returns KC_EINVAL for an unknown knob or a value out of range.
+ */
+#define KC_PARAM_SMEM_MAX_WORDS 1
+kc_status kc_set_param(int param, int64_t value);
+kc_status kc_get_param(int param, int64_t* value);
+
+/*
+ * kc_count_csr / kc_estimate_csr -- one-shot forms: kc_orient, then kc_count
+ * (or kc_estimate), then kc_free.  Arguments as above; KC_DEVICE_PTRS
+ * applies to the inputs and the outputs alike.
+ */
+kc_status kc_count_csr(const int64_t* off, const int32_t* adj, int32_t n, int64_t m, int k,
+                       unsigned flags, uint64_t* total, uint64_t* per_vertex,
+                       uint64_t* per_owner, void* stream);
+kc_status kc_estimate_csr(const int64_t* off, const int32_t* adj, int32_t n, int64_t m,
+                          int k, uint32_t colours, uint64_t seed, unsigned flags,
+                          uint64_t* sampled, double* estimate, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KC_H */

@@ -1,0 +1,366 @@
+// api.cu -- the extern "C" entry points of libkc (declared in include/kc.h).
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "kc_internal.cuh"
+
+namespace kc {
+
+kc_status orient(const int64_t* off, const int32_t* adj, int32_t n, int64_t m, unsigned flags,
+                 cudaStream_t s, kc_graph** out);
+int num_sms();
+
+namespace {
+
+thread_local char g_cuda_err[256] = "no error";
+
+// out[perm[r]] = in[r]  (rank space -> caller ids)
+__global__ void k_permute_u64(const unsigned long long* __restrict__ in, const int32_t* __restrict__ perm,
+                              int32_t n, unsigned long long* __restrict__ out)
+{
+    for (int32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x)
+        out[perm[r]] = in[r];
+}
+
+__global__ void k_permute_i32_to_u64(const int32_t* __restrict__ in, const int32_t* __restrict__ perm,
+                                     int32_t n, unsigned long long* __restrict__ out)
+{
+    for (int32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x)
+        out[perm[r]] = (unsigned long long)in[r];
+}
+
+__global__ void k_fill_u64(unsigned long long* __restrict__ out, int32_t n, unsigned long long v)
+{
+    for (int32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) out[r] = v;
+}
+
+int grid1d(int64_t n)
+{
+    int64_t g = (n + 255) / 256;
+    const int64_t cap = (int64_t)num_sms() * 8;
+    if (g > cap) g = cap;
+    return (int)(g < 1 ? 1 : g);
+}
+
+// Stream-ordered scratch, released on scope exit (after the stream's work).
+struct Scratch {
+    cudaStream_t s;
+    std::vector<void*> ptrs;
+    explicit Scratch(cudaStream_t st) : s(st) {}
+    ~Scratch()
+    {
+        for (void* p : ptrs) cudaFreeAsync(p, s);
+    }
+    template <typename T>
+    kc_status get(T** p, int64_t count)
+    {
+        void* q = nullptr;
+        cudaError_t e = cudaMallocAsync(&q, (size_t)std::max<int64_t>(count, 1) * sizeof(T), s);
+        if (e != cudaSuccess) {
+            set_cuda_error(e, "cudaMallocAsync");
+            return e == cudaErrorMemoryAllocation ? KC_ENOMEM : KC_ECUDA;
+        }
+        ptrs.push_back(q);
+        *p = (T*)q;
+        return KC_OK;
+    }
+};
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+// Host-ordered output of an n-array: device array `src` -> `dst` (host or
+// device per `dev`).
+kc_status copy_out_u64(uint64_t* dst, const unsigned long long* src, int32_t n, bool dev, cudaStream_t s)
+{
+    if (!dst || n <= 0) return KC_OK;
+    KC_CK(cudaMemcpyAsync(dst, src, (size_t)n * sizeof(uint64_t),
+                          dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    return KC_OK;
+}
+
+// Shared body of kc_count and kc_estimate.
+kc_status run_count(const kc_graph* g, int k, uint32_t colours, uint64_t seed, unsigned flags,
+                    uint64_t* total, uint64_t* per_vertex, uint64_t* per_owner, cudaStream_t s)
+{
+    const bool dev = (flags & KC_DEVICE_PTRS) != 0;
+    const int32_t n = g->n;
+    Scratch sc(s);
+    unsigned long long* small = nullptr;  // [0..1] total lo/hi, [2..9] cursors
+    KC_TRY(sc.get(&small, 16));
+    KC_CK(cudaMemsetAsync(small, 0, 16 * sizeof(unsigned long long), s));
+
+    // outputs: write permuted results straight into device outputs, else into temps
+    unsigned long long* out_pv = nullptr;
+    unsigned long long* out_po = nullptr;
+    if (per_vertex) {
+        if (dev) out_pv = (unsigned long long*)per_vertex;
+        else KC_TRY(sc.get(&out_pv, n));
+    }
+    if (per_owner) {
+        if (dev) out_po = (unsigned long long*)per_owner;
+        else KC_TRY(sc.get(&out_po, n));
+    }
+
+    if (k <= 2) {
+        const unsigned long long q = k == 1 ? (unsigned long long)n : (unsigned long long)g->m;
+        k_fill_u64<<<1, 32, 0, s>>>(small, 1, q);
+        KC_CK(cudaGetLastError());
+        if (n > 0) {
+            if (out_pv) {
+                if (k == 1) k_fill_u64<<<grid1d(n), 256, 0, s>>>(out_pv, n, 1ull);
+                else k_permute_i32_to_u64<<<grid1d(n), 256, 0, s>>>(g->deg, g->perm, n, out_pv);
+                KC_CK(cudaGetLastError());
+            }
+            if (out_po) {
+                if (k == 1) k_fill_u64<<<grid1d(n), 256, 0, s>>>(out_po, n, 1ull);
+                else k_permute_i32_to_u64<<<grid1d(n), 256, 0, s>>>(g->dplus, g->perm, n, out_po);
+                KC_CK(cudaGetLastError());
+            }
+        }
+    } else if (n > 0) {
+        unsigned long long* pv_rank = nullptr;
+        unsigned long long* po_rank = nullptr;
+        if (per_vertex) {
+            KC_TRY(sc.get(&pv_rank, n));
+            KC_CK(cudaMemsetAsync(pv_rank, 0, (size_t)n * sizeof(unsigned long long), s));
+        }
+        if (per_owner) {
+            KC_TRY(sc.get(&po_rank, n));
+            KC_CK(cudaMemsetAsync(po_rank, 0, (size_t)n * sizeof(unsigned long long), s));
+        }
+        int slots = 0;
+        const int64_t hw = heavy_scratch_words(g, k, &slots);
+        uint32_t* heavy = nullptr;
+        if (hw > 0) KC_TRY(sc.get(&heavy, hw));
+        CountArgs a;
+        a.k = k;
+        a.colours = colours;
+        a.seed = seed;
+        a.per_vertex = per_vertex != nullptr;
+        a.total = small;
+        a.pv = pv_rank;
+        a.po = po_rank;
+        KC_TRY(count_launch(g, a, small + 2, heavy, hw, s));
+        if (pv_rank) {
+            k_permute_u64<<<grid1d(n), 256, 0, s>>>(pv_rank, g->perm, n, out_pv);
+            KC_CK(cudaGetLastError());
+        }
+        if (po_rank) {
+            k_permute_u64<<<grid1d(n), 256, 0, s>>>(po_rank, g->perm, n, out_po);
+            KC_CK(cudaGetLastError());
+        }
+    }
+
+    if (dev) {
+        KC_CK(cudaMemcpyAsync(total, small, 2 * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+        return KC_OK;
+    }
+    unsigned long long th[2] = {0, 0};
+    KC_CK(cudaMemcpyAsync(th, small, sizeof(th), cudaMemcpyDeviceToHost, s));
+    KC_TRY(copy_out_u64(per_vertex, out_pv, n, false, s));
+    KC_TRY(copy_out_u64(per_owner, out_po, n, false, s));
+    KC_CK(cudaStreamSynchronize(s));
+    *total = th[0];
+    return th[1] ? KC_EOVERFLOW : KC_OK;
+}
+
+}  // namespace
+
+void set_cuda_error(cudaError_t e, const char* what)
+{
+    std::snprintf(g_cuda_err, sizeof(g_cuda_err), "%s: %s (%d)", what, cudaGetErrorString(e), (int)e);
+}
+
+}  // namespace kc
+
+extern "C" {
+
+const char* kc_strerror(kc_status s)
+{
+    switch (s) {
+    case KC_OK: return "ok";
+    case KC_EINVAL: return "invalid argument";
+    case KC_ENOMEM: return "out of memory";
+    case KC_EOVERFLOW: return "count overflow";
+    case KC_ETIMEOUT: return "device wait timed out";
+    case KC_ECUDA: return "CUDA error";
+    case KC_ENOTSUP: return "not supported";
+    }
+    return "unknown status";
+}
+
+const char* kc_last_cuda_error(void) { return kc::g_cuda_err; }
+
+const char* kc_version(void) { return "kc 0.1 sm_103a"; }
+
+kc_status kc_build_csr(int32_t n, const int32_t* src, const int32_t* dst, int64_t ne, int64_t* off,
+                       int32_t* adj, int64_t* m_out)
+{
+    if (n < 0 || ne < 0 || !off || !m_out || (ne > 0 && (!src || !dst || !adj))) return KC_EINVAL;
+    std::vector<uint64_t> keys;
+    try {
+        keys.reserve((size_t)ne * 2);
+    } catch (...) {
+        return KC_ENOMEM;
+    }
+    for (int64_t i = 0; i < ne; ++i) {
+        const int32_t a = src[i], b = dst[i];
+        if (a < 0 || a >= n || b < 0 || b >= n) return KC_EINVAL;
+        if (a == b) continue;
+        keys.push_back(((uint64_t)(uint32_t)a << 32) | (uint32_t)b);
+        keys.push_back(((uint64_t)(uint32_t)b << 32) | (uint32_t)a);
+    }
+    std::sort(keys.begin(), keys.end());
+    keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
+    std::fill(off, off + (size_t)n + 1, 0);
+    for (size_t i = 0; i < keys.size(); ++i) {
+        off[(keys[i] >> 32) + 1]++;
+        adj[i] = (int32_t)(keys[i] & 0xffffffffu);
+    }
+    for (int32_t v = 0; v < n; ++v) off[v + 1] += off[v];
+    *m_out = (int64_t)keys.size() / 2;
+    return KC_OK;
+}
+
+kc_status kc_orient(const int64_t* off, const int32_t* adj, int32_t n, int64_t m, unsigned flags, void* stream,
+                    kc_graph** out)
+{
+    if (!out) return KC_EINVAL;
+    *out = nullptr;
+    return kc::orient(off, adj, n, m, flags, (cudaStream_t)stream, out);
+}
+
+void kc_free(kc_graph* g)
+{
+    if (!g) return;
+    kc::DeviceGuard dg(g->device);
+    cudaFree(g->rank);
+    cudaFree(g->perm);
+    cudaFree(g->deg);
+    cudaFree(g->dplus);
+    cudaFree(g->offp);
+    cudaFree(g->adjp);
+    cudaFree(g->queue);
+    delete g;
+}
+
+kc_status kc_info(const kc_graph* g, kc_graph_info* info)
+{
+    if (!g || !info) return KC_EINVAL;
+    info->n = g->n;
+    info->m = g->m;
+    info->max_dplus = g->max_dplus;
+    info->wedges = g->wedges;
+    info->device_bytes = g->bytes;
+    return KC_OK;
+}
+
+kc_status kc_export(const kc_graph* g, unsigned flags, int32_t* rank, int32_t* perm, int64_t* off_plus,
+                    int32_t* adj_plus, int32_t* queue, void* stream)
+{
+    if (!g) return KC_EINVAL;
+    kc::DeviceGuard dg(g->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const cudaMemcpyKind kind = (flags & KC_DEVICE_PTRS) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    const size_t n = (size_t)g->n;
+    if (rank && n) KC_CK(cudaMemcpyAsync(rank, g->rank, n * sizeof(int32_t), kind, s));
+    if (perm && n) KC_CK(cudaMemcpyAsync(perm, g->perm, n * sizeof(int32_t), kind, s));
+    if (off_plus) KC_CK(cudaMemcpyAsync(off_plus, g->offp, (n + 1) * sizeof(int64_t), kind, s));
+    if (adj_plus && g->m) KC_CK(cudaMemcpyAsync(adj_plus, g->adjp, (size_t)g->m * sizeof(int32_t), kind, s));
+    if (queue && n) KC_CK(cudaMemcpyAsync(queue, g->queue, n * sizeof(int32_t), kind, s));
+    KC_CK(cudaStreamSynchronize(s));
+    return KC_OK;
+}
+
+kc_status kc_count(const kc_graph* g, int k, unsigned flags, uint64_t* total, uint64_t* per_vertex,
+                   uint64_t* per_owner, void* stream)
+{
+    if (!g || !total || k < 1 || k > KC_MAX_K) return KC_EINVAL;
+    kc::DeviceGuard dg(g->device);
+    return kc::run_count(g, k, 0, 0, flags, total, per_vertex, per_owner, (cudaStream_t)stream);
+}
+
+kc_status kc_estimate(const kc_graph* g, int k, uint32_t colours, uint64_t seed, unsigned flags,
+                      uint64_t* sampled, double* estimate, uint64_t* per_owner, void* stream)
+{
+    if (!g || !sampled || k < 1 || k > KC_MAX_K || colours < 1) return KC_EINVAL;
+    kc::DeviceGuard dg(g->device);
+    kc_status st = kc::run_count(g, k, colours, seed, flags, sampled, nullptr, per_owner, (cudaStream_t)stream);
+    if (st != KC_OK) return st;
+    if (estimate && !(flags & KC_DEVICE_PTRS)) {
+        double f = 1.0;
+        for (int i = 0; i < k - 2; ++i) f *= (double)colours;
+        *estimate = (double)*sampled * f;
+    }
+    return KC_OK;
+}
+
+kc_status kc_set_param(int param, int64_t value)
+{
+    if (param == KC_PARAM_SMEM_MAX_WORDS) return kc::set_smem_max_words(value);
+    return KC_EINVAL;
+}
+
+kc_status kc_get_param(int param, int64_t* value)
+{
+    if (!value) return KC_EINVAL;
+    if (param == KC_PARAM_SMEM_MAX_WORDS) {
+        *value = kc::smem_max_words();
+        return KC_OK;
+    }
+    return KC_EINVAL;
+}
+
+kc_status kc_count_csr(const int64_t* off, const int32_t* adj, int32_t n, int64_t m, int k, unsigned flags,
+                       uint64_t* total, uint64_t* per_vertex, uint64_t* per_owner, void* stream)
+{
+    kc_graph* g = nullptr;
+    kc_status st = kc_orient(off, adj, n, m, flags, stream, &g);
+    if (st != KC_OK) return st;
+    st = kc_count(g, k, flags, total, per_vertex, per_owner, stream);
+    if (st == KC_OK && (flags & KC_DEVICE_PTRS)) {
+        cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+        if (e != cudaSuccess) {
+            kc::set_cuda_error(e, "cudaStreamSynchronize");
+            st = KC_ECUDA;
+        }
+    }
+    kc_free(g);
+    return st;
+}
+
+kc_status kc_estimate_csr(const int64_t* off, const int32_t* adj, int32_t n, int64_t m, int k, uint32_t colours,
+                          uint64_t seed, unsigned flags, uint64_t* sampled, double* estimate, void* stream)
+{
+    kc_graph* g = nullptr;
+    kc_status st = kc_orient(off, adj, n, m, flags, stream, &g);
+    if (st != KC_OK) return st;
+    st = kc_estimate(g, k, colours, seed, flags, sampled, estimate, nullptr, stream);
+    if (st == KC_OK && (flags & KC_DEVICE_PTRS)) {
+        cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+        if (e != cudaSuccess) {
+            kc::set_cuda_error(e, "cudaStreamSynchronize");
+            st = KC_ECUDA;
+        }
+    }
+    kc_free(g);
+    return st;
+}
+
+}  // extern "C"

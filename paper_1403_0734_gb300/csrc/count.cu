@@ -1,0 +1,617 @@
+// count.cu -- Rounds 2-3 of Algorithm 1 (Sec. 3) and the colour filter of
+// cFFF_k (Sec. 6) on the device.
+//
+// For every owner u (rank r) with d = |Gamma+(u)| >= k-1:
+//   (b) build G+(u) as a bitmap: local ids 0..d-1 are the positions of
+//       Gamma+(u) in the order; bit j of row i is set iff x_j is in
+//       Gamma+(x_i) -- exactly the pairs x_i < x_j that Map 2 emits and
+//       Reduce 2 keeps because they are edges.  Each Gamma+(x_i) list is
+//       streamed and its entries are searched in the sorted Gamma+(u); the
+//       scan stops at max Gamma+(u).  With per-vertex counts the bitmap is
+//       kept symmetric (bit i of row j too).
+//   (d) cFFF_k: a pair is kept only if colour(u, x_i) == colour(u, x_j).
+//   (c) count the (k-1)-cliques of G+(u) (Reduce 3) by a depth-first
+//       search that ANDs rows: a chain i1 < i2 < ... with candidate set
+//       C_t = C_{t-1} & row(i_t) restricted to ids above i_t.  The last two
+//       levels are closed in one step: with C the candidates after k-3
+//       choices, the cliques completed are the edges inside C,
+//       sum_{e in C} popc(C & row_up(e)), and (per-vertex mode) vertex e of C
+//       lies in popc(C & row(e)) of them -- no per-clique work.
+//       Chain members and u are credited with the sub-tree totals.
+// Owners come from the queue (|Gamma+| descending) in classes by bitmap
+// width W = ceil(d/32): W = 1 runs one warp per owner with the rows in
+// registers; W in {2..32} one CTA per owner with the rows in shared memory;
+// wider owners use the same CTA code on a global-memory tile.
+#include <algorithm>
+#include <climits>
+
+#include "kc_internal.cuh"
+
+namespace kc {
+
+int num_sms();
+
+// Process-wide knob: widest bitmap row (in 32-bit words) kept in shared memory.
+static int g_smem_max_words = kNumSmemClasses > 0 ? kClassWords[kNumSmemClasses - 1] : 1;
+
+int smem_max_words() { return g_smem_max_words; }
+
+kc_status set_smem_max_words(int64_t v)
+{
+    if (v < 1 || v > kClassWords[kNumSmemClasses - 1]) return KC_EINVAL;
+    g_smem_max_words = (int)v;
+    return KC_OK;
+}
+
+namespace {
+
+struct Ctx {
+    const int64_t* __restrict__ offp;
+    const int32_t* __restrict__ adjp;
+    const int32_t* __restrict__ queue;
+    const int32_t* __restrict__ perm;
+    int64_t q0, q1;
+    int k;
+    uint32_t colours;
+    uint64_t seed;
+    unsigned long long* total;
+    unsigned long long* pv;
+    unsigned long long* po;
+    unsigned long long* cursor;
+};
+
+// colour(u, x): splitmix64 output function over seed ^ (G * (u<<32 | x)),
+// reduced to [0, c) by a 64x64 multiply-high (Sec. 6; spec in kc.h).
+__device__ __forceinline__ uint32_t colour_of(uint64_t seed, int32_t u, int32_t x, uint32_t c)
+{
+    uint64_t key = ((uint64_t)(uint32_t)u << 32) | (uint64_t)(uint32_t)x;
+    uint64_t z = seed ^ (0x9E3779B97F4A7C15ull * key);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return (uint32_t)__umul64hi(z, (uint64_t)c);
+}
+
+// 128-bit total as (lo, hi) words.
+__device__ __forceinline__ void add_total(unsigned long long* t, unsigned long long v)
+{
+    if (v == 0) return;
+    unsigned long long old = atomicAdd(&t[0], v);
+    if (old + v < old) atomicAdd(&t[1], 1ull);
+}
+
+__device__ __forceinline__ unsigned long long warp_sum64(unsigned long long v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+__device__ __forceinline__ uint32_t mask_above(int b) { return b >= 31 ? 0u : (kFull << (b + 1)); }
+__device__ __forceinline__ uint32_t mask_below(int b) { return (1u << b) - 1u; }
+
+// ------------------------------------------------------------ W = 1 class
+
+// Edges inside C (one word; lane l owns local vertex l).  pvl += degree of
+// the lane's vertex inside C (per-vertex mode).
+template <bool PV>
+__device__ __forceinline__ unsigned long long leaf2_w1(uint32_t C, uint32_t up, uint32_t A, int lane,
+                                                       unsigned long long& pvl)
+{
+    const bool in = (C >> lane) & 1u;
+    const uint32_t e = in ? (uint32_t)__popc(C & up) : 0u;
+    if (PV && in) pvl += (unsigned long long)__popc(C & A);
+    return (unsigned long long)__reduce_add_sync(kFull, e);
+}
+
+template <bool PV, bool COL>
+__global__ void __launch_bounds__(256) k_count_w1(Ctx c)
+{
+    const int lane = threadIdx.x & 31;
+    const int r0 = c.k - 1;  // vertices to choose inside G+(u)
+    for (;;) {
+        unsigned long long pos = 0;
+        if (lane == 0) pos = atomicAdd(c.cursor, 1ull);
+        pos = __shfl_sync(kFull, pos, 0);
+        const int64_t q = c.q0 + (int64_t)pos;
+        if (q >= c.q1) break;
+        const int32_t r = c.queue[q];
+        const int64_t b = c.offp[r];
+        const int d = (int)(c.offp[r + 1] - b);
+        const int32_t x = lane < d ? c.adjp[b + lane] : INT_MAX;
+        const int32_t maxL = __shfl_sync(kFull, x, d - 1);
+        uint32_t col = 0;
+        if (COL && lane < d) col = colour_of(c.seed, c.perm[r], c.perm[x], c.colours);
+
+        // (b) rows: lane j searches x_j in each 32-entry chunk of Gamma+(x_i)
+        uint32_t up = 0;
+        for (int i = 0; i < d - 1; ++i) {
+            const int32_t xi = __shfl_sync(kFull, x, i);
+            const int64_t s0 = c.offp[xi], s1 = c.offp[xi + 1];
+            uint32_t row = 0;
+            for (int64_t p0 = s0; p0 < s1; p0 += 32) {
+                const int64_t p = p0 + lane;
+                const int32_t y = p < s1 ? c.adjp[p] : INT_MAX;
+                int lo = 0;
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1) {
+                    const int32_t yy = __shfl_sync(kFull, y, lo + step - 1);
+                    if (yy < x) lo += step;
+                }
+                const int32_t yl = __shfl_sync(kFull, y, lo);
+                row |= __ballot_sync(kFull, lane > i && lane < d && yl == x);
+                if (__shfl_sync(kFull, y, 31) >= maxL) break;
+            }
+            if (COL) row &= __ballot_sync(kFull, col == __shfl_sync(kFull, col, i));
+            if (lane == i) up = row;
+        }
+        uint32_t A = up;
+        if (PV) {
+            uint32_t low = 0;
+            for (int j = 1; j < d; ++j) {
+                const uint32_t colj = __ballot_sync(kFull, (up >> j) & 1u);
+                if (lane == j) low = colj;
+            }
+            A = up | low;
+        }
+
+        // (c) depth-first search; level t's state of the chain is kept in lane t
+        unsigned long long tot = 0, pvl = 0;
+        const uint32_t C1 = d >= 32 ? kFull : ((1u << d) - 1u);
+        if (r0 == 2) {
+            tot = leaf2_w1<PV>(C1, up, A, lane, pvl);
+        } else {
+            uint32_t st_rem = 0;
+            int st_e = 0;
+            unsigned long long st_sub = 0;
+            int t = 0;
+            uint32_t cur = C1;
+            unsigned long long cur_sub = 0;
+            for (;;) {
+                if (cur == 0) {
+                    if (t == 0) break;
+                    const unsigned long long sdone = cur_sub;
+                    --t;
+                    cur = __shfl_sync(kFull, st_rem, t);
+                    const int pe = __shfl_sync(kFull, st_e, t);
+                    cur_sub = __shfl_sync(kFull, st_sub, t) + sdone;
+                    if (PV && lane == pe) pvl += sdone;
+                    continue;
+                }
+                const int e = __ffs(cur) - 1;
+                cur &= cur - 1u;
+                const uint32_t Cn = cur & __shfl_sync(kFull, up, e);
+                const int need = r0 - t - 1;
+                if (__popc(Cn) < need) continue;
+                if (need == 2) {
+                    const unsigned long long E = leaf2_w1<PV>(Cn, up, A, lane, pvl);
+                    tot += E;
+                    cur_sub += E;
+                    if (PV && lane == e) pvl += E;
+                } else {
+                    if (lane == t) {
+                        st_rem = cur;
+                        st_e = e;
+                        st_sub = cur_sub;
+                    }
+                    ++t;
+                    cur = Cn;
+                    cur_sub = 0;
+                }
+            }
+        }
+        if (lane == 0) {
+            add_total(c.total, tot);
+            if (c.po) c.po[r] = tot;
+            if (PV && tot) atomicAdd(&c.pv[r], tot);
+        }
+        if (PV && lane < d && pvl) atomicAdd(&c.pv[x], pvl);
+    }
+}
+
+// ----------------------------------------------------- wide classes (CTA)
+
+// Next element (ascending) of the word set `set` from word `low`; removes it.
+__device__ __forceinline__ int warp_next(uint32_t* set, int& low, int W, int lane)
+{
+    while (low < W) {
+        const int w = low + lane;
+        const uint32_t v = w < W ? set[w] : 0u;
+        const uint32_t nz = __ballot_sync(kFull, v != 0u);
+        if (nz) {
+            const int f = __ffs(nz) - 1;
+            const uint32_t vf = __shfl_sync(kFull, v, f);
+            const int e = (low + f) * 32 + __ffs(vf) - 1;
+            __syncwarp();
+            if (lane == 0) set[low + f] = vf & (vf - 1u);
+            __syncwarp();
+            low += f;
+            return e;
+        }
+        low += 32;
+    }
+    return -1;
+}
+
+// out = a & b over words [low, W); returns the population count.
+__device__ __forceinline__ int warp_and(const uint32_t* a, const uint32_t* b, uint32_t* out, int low, int W,
+                                        int lane)
+{
+    int cnt = 0;
+    for (int w = low + lane; w < W; w += 32) {
+        const uint32_t v = a[w] & b[w];
+        out[w] = v;
+        cnt += __popc(v);
+    }
+    __syncwarp();
+    return (int)__reduce_add_sync(kFull, (unsigned)cnt);
+}
+
+// Edges inside the word set C (words [low, W)); per-vertex mode adds each
+// element's degree inside C to pv.
+template <bool PV>
+__device__ unsigned long long warp_leaf2(const uint32_t* C, int low, int W, const uint32_t* A, int RS,
+                                         int32_t* el, unsigned long long* pv, int lane)
+{
+    int nel = 0, hiw = low;
+    const uint32_t lt = mask_below(lane);
+    for (int w0 = low; w0 < W; w0 += 32) {
+        const int w = w0 + lane;
+        const uint32_t v = w < W ? C[w] : 0u;
+        uint32_t nz = __ballot_sync(kFull, v != 0u);
+        while (nz) {
+            const int f = __ffs(nz) - 1;
+            nz &= nz - 1u;
+            const uint32_t bits = __shfl_sync(kFull, v, f);
+            if ((bits >> lane) & 1u) el[nel + __popc(bits & lt)] = (w0 + f) * 32 + lane;
+            nel += __popc(bits);
+            hiw = w0 + f + 1;
+        }
+    }
+    __syncwarp();
+    unsigned long long E = 0;
+    for (int p = lane; p < nel; p += 32) {
+        const int e = el[p];
+        const int we = e >> 5, be = e & 31;
+        const uint32_t* Ae = A + (int64_t)e * RS;
+        uint32_t cnt = (uint32_t)__popc(C[we] & Ae[we] & mask_above(be));
+        for (int w = we + 1; w < hiw; ++w) cnt += (uint32_t)__popc(C[w] & Ae[w]);
+        E += cnt;
+        if (PV) {
+            uint32_t lowc = (uint32_t)__popc(C[we] & Ae[we] & mask_below(be));
+            for (int w = low; w < we; ++w) lowc += (uint32_t)__popc(C[w] & Ae[w]);
+            if (cnt + lowc) atomicAdd(&pv[e], (unsigned long long)(cnt + lowc));
+        }
+    }
+    __syncwarp();
+    return warp_sum64(E);
+}
+
+// Depth-first search below a chosen prefix.  stk level 0 holds the candidate
+// set (elements above the prefix's last vertex, starting at word low0);
+// need0 >= 3 vertices are still to be chosen.  Chain state of level t lives
+// in lane t.  Returns the number of cliques completed in the sub-tree and
+// credits chain members inside it.
+template <bool PV>
+__device__ unsigned long long warp_dfs(uint32_t* stk, int SW, int W, int low0, int need0, const uint32_t* A,
+                                       int RS, int32_t* el, unsigned long long* pv, int lane)
+{
+    unsigned long long total = 0, cur_sub = 0, st_sub = 0;
+    int t = 0, low = low0, st_low = 0, st_e = 0;
+    for (;;) {
+        const int e = warp_next(stk + (int64_t)t * SW, low, W, lane);
+        if (e < 0) {
+            if (t == 0) break;
+            const unsigned long long sdone = cur_sub;
+            --t;
+            low = __shfl_sync(kFull, st_low, t);
+            const int pe = __shfl_sync(kFull, st_e, t);
+            cur_sub = __shfl_sync(kFull, st_sub, t) + sdone;
+            if (PV && lane == 0 && sdone) atomicAdd(&pv[pe], sdone);
+            continue;
+        }
+        const int need = need0 - t - 1;
+        const int we = e >> 5;
+        const int cnt = warp_and(stk + (int64_t)t * SW, A + (int64_t)e * RS, stk + (int64_t)(t + 1) * SW, we, W, lane);
+        if (cnt < need) continue;
+        if (need == 2) {
+            const unsigned long long E = warp_leaf2<PV>(stk + (int64_t)(t + 1) * SW, we, W, A, RS, el, pv, lane);
+            total += E;
+            cur_sub += E;
+            if (PV && lane == 0 && E) atomicAdd(&pv[e], E);
+        } else {
+            if (lane == t) {
+                st_low = low;
+                st_e = e;
+                st_sub = cur_sub;
+            }
+            ++t;
+            low = we;
+            cur_sub = 0;
+        }
+    }
+    return total;
+}
+
+// Layout of the per-CTA working set (shared memory, or a global slot for the
+// heavy class).  All sizes in 32-bit words.
+struct Layout {
+    int64_t L, col, pv, A, stk, el, total;
+};
+
+__host__ __device__ inline Layout make_layout(int W, int RS, int NW, int levels, bool pv, bool col)
+{
+    const int64_t D = 32LL * W;
+    Layout l;
+    l.L = 0;
+    l.col = l.L + D;
+    l.pv = l.col + (col ? D : 0);
+    l.A = l.pv + (pv ? 2 * D : 0);
+    l.stk = l.A + D * RS;
+    l.el = l.stk + (int64_t)NW * levels * W;
+    l.total = l.el + (int64_t)NW * D;
+    return l;
+}
+
+template <bool PV, bool COL, bool HEAVY>
+__global__ void __launch_bounds__(256) k_count_cta(Ctx c, int W, int levels, uint32_t* gscratch,
+                                                   int64_t slot_words)
+{
+    extern __shared__ __align__(16) uint32_t smem[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, NW = blockDim.x >> 5;
+    const int RS = HEAVY ? W : W + 1;
+    const Layout lay = make_layout(W, RS, NW, levels, PV, COL);
+    uint32_t* base = HEAVY ? gscratch + (int64_t)blockIdx.x * slot_words : smem;
+    int32_t* sL = (int32_t*)(base + lay.L);
+    uint32_t* sCol = base + lay.col;
+    unsigned long long* sPV = (unsigned long long*)(base + lay.pv);
+    uint32_t* sA = base + lay.A;
+    uint32_t* stk = base + lay.stk + (int64_t)wid * levels * W;
+    int32_t* el = (int32_t*)(base + lay.el) + (int64_t)wid * 32 * W;
+    __shared__ int s_next;
+    __shared__ unsigned long long s_tot;
+    __shared__ long long s_item;
+
+    const int r0 = c.k - 1;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (long long)atomicAdd(c.cursor, 1ull);
+        __syncthreads();
+        const int64_t q = c.q0 + s_item;
+        if (q >= c.q1) break;
+        const int32_t r = c.queue[q];
+        const int64_t b = c.offp[r];
+        const int d = (int)(c.offp[r + 1] - b);
+        const int32_t ur = COL ? c.perm[r] : 0;
+        for (int j = threadIdx.x; j < d; j += blockDim.x) {
+            const int32_t x = c.adjp[b + j];
+            sL[j] = x;
+            if (COL) sCol[j] = colour_of(c.seed, ur, c.perm[x], c.colours);
+            if (PV) sPV[j] = 0ull;
+        }
+        for (int64_t j = threadIdx.x; j < (int64_t)d * RS; j += blockDim.x) sA[j] = 0u;
+        if (threadIdx.x == 0) {
+            s_next = 0;
+            s_tot = 0ull;
+        }
+        __syncthreads();
+        const int32_t maxL = sL[d - 1];
+        const int Wd = (d + 31) >> 5;  // words in use by this owner
+
+        // (b) + (d): rows, split over warps
+        for (int i = wid; i < d - 1; i += NW) {
+            const int32_t xi = sL[i];
+            const int64_t s0 = c.offp[xi], s1 = c.offp[xi + 1];
+            const uint32_t ci = COL ? sCol[i] : 0u;
+            for (int64_t p0 = s0; p0 < s1; p0 += 32) {
+                const int64_t pp = p0 + lane;
+                const int32_t y = pp < s1 ? c.adjp[pp] : INT_MAX;
+                if (y <= maxL) {
+                    int lo = i + 1, hi = d;
+                    while (lo < hi) {
+                        const int mid = (lo + hi) >> 1;
+                        if (sL[mid] < y) lo = mid + 1; else hi = mid;
+                    }
+                    if (lo < d && sL[lo] == y && (!COL || sCol[lo] == ci)) {
+                        atomicOr(&sA[(int64_t)i * RS + (lo >> 5)], 1u << (lo & 31));
+                        if (PV) atomicOr(&sA[(int64_t)lo * RS + (i >> 5)], 1u << (i & 31));
+                    }
+                }
+                if (__shfl_sync(kFull, y, 31) >= maxL) break;
+            }
+        }
+        __syncthreads();
+
+        // (c) count
+        unsigned long long wtot = 0;
+        if (r0 == 2) {
+            for (int e = wid; e < d; e += NW) {
+                const uint32_t* Ae = sA + (int64_t)e * RS;
+                const int we = e >> 5, be = e & 31;
+                unsigned up = 0, all = 0;
+                for (int w = we + lane; w < Wd; w += 32) {
+                    const uint32_t v = Ae[w];
+                    up += (unsigned)__popc(w == we ? (v & mask_above(be)) : v);
+                }
+                if (PV)
+                    for (int w = lane; w < Wd; w += 32) all += (unsigned)__popc(Ae[w]);
+                up = __reduce_add_sync(kFull, up);
+                wtot += up;
+                if (PV) {
+                    all = __reduce_add_sync(kFull, all);
+                    if (lane == 0 && all) sPV[e] += all;
+                }
+            }
+        } else {
+            const int need0 = r0 - 1;
+            for (;;) {
+                int e1 = 0;
+                if (lane == 0) e1 = atomicAdd(&s_next, 1);
+                e1 = __shfl_sync(kFull, e1, 0);
+                if (e1 >= d) break;
+                const int we = e1 >> 5, be = e1 & 31;
+                const uint32_t* Ae = sA + (int64_t)e1 * RS;
+                int cnt = 0;
+                for (int w = we + lane; w < Wd; w += 32) {
+                    uint32_t v = Ae[w];
+                    if (w == we) v &= mask_above(be);
+                    stk[w] = v;
+                    cnt += __popc(v);
+                }
+                __syncwarp();
+                cnt = (int)__reduce_add_sync(kFull, (unsigned)cnt);
+                if (cnt < need0) continue;
+                const unsigned long long sub =
+                    need0 == 2 ? warp_leaf2<PV>(stk, we, Wd, sA, RS, el, sPV, lane)
+                               : warp_dfs<PV>(stk, W, Wd, we, need0, sA, RS, el, sPV, lane);
+                wtot += sub;
+                if (PV && lane == 0 && sub) atomicAdd(&sPV[e1], sub);
+            }
+        }
+        if (lane == 0 && wtot) atomicAdd(&s_tot, wtot);
+        __syncthreads();
+        const unsigned long long tot = s_tot;
+        if (threadIdx.x == 0) {
+            add_total(c.total, tot);
+            if (c.po) c.po[r] = tot;
+            if (PV && tot) atomicAdd(&c.pv[r], tot);
+        }
+        if (PV)
+            for (int j = threadIdx.x; j < d; j += blockDim.x) {
+                const unsigned long long v = sPV[j];
+                if (v) atomicAdd(&c.pv[sL[j]], v);
+            }
+        __syncthreads();
+    }
+}
+
+template <typename K>
+int blocks_per_sm(K kernel, int threads, size_t smem)
+{
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, smem) != cudaSuccess || nb < 1)
+        nb = 1;
+    return nb;
+}
+
+int warps_for_width(int W)
+{
+    if (W <= 2) return 2;
+    if (W <= 4) return 4;
+    return 8;
+}
+
+template <bool PV, bool COL>
+kc_status launch_classes(const kc_graph* g, Ctx base, unsigned long long* cursors, uint32_t* heavy,
+                         int64_t heavy_words, cudaStream_t s)
+{
+    const int sms = num_sms();
+    const int k = base.k;
+    const int levels = k > 3 ? k - 3 : 1;
+    auto ge_at = [&](int64_t t) -> int64_t {
+        if (t <= 0) return g->n;
+        return t <= (int64_t)g->max_dplus ? g->ge[(size_t)t] : 0;
+    };
+    const int64_t dmin = k - 1;  // Reduce 1 filter
+    const int maxw = smem_max_words();
+    int ci = 0;
+
+    // heavy: rows wider than the shared-memory limit, global tiles
+    {
+        const int64_t q1 = ge_at(std::max<int64_t>(32LL * maxw + 1, dmin)), q0 = 0;
+        if (q1 > q0) {
+            const int W = (g->max_dplus + 31) / 32;
+            const int NW = 8;
+            const Layout lay = make_layout(W, W, NW, levels, PV, COL);
+            const int64_t slot = lay.total;
+            const int64_t slots = heavy_words / slot;
+            if (slots < 1) return KC_ENOMEM;
+            Ctx c = base;
+            c.q0 = q0;
+            c.q1 = q1;
+            c.cursor = cursors + ci++;
+            const int grid = (int)std::min<int64_t>(std::min<int64_t>(slots, q1 - q0), sms);
+            k_count_cta<PV, COL, true><<<grid, NW * 32, 0, s>>>(c, W, levels, heavy, slot);
+            KC_CK(cudaGetLastError());
+        }
+    }
+    // shared-memory classes, widest first
+    for (int cl = kNumSmemClasses - 1; cl >= 1; --cl) {
+        const int W = kClassWords[cl];
+        if (W > maxw) continue;
+        const int64_t dlo = 32LL * kClassWords[cl - 1] + 1, dhi = 32LL * W;
+        const int64_t q0 = ge_at(dhi + 1), q1 = ge_at(std::max(dlo, dmin));
+        if (q1 <= q0) continue;
+        const int NW = warps_for_width(W);
+        const Layout lay = make_layout(W, W + 1, NW, levels, PV, COL);
+        const size_t smem = (size_t)lay.total * 4;
+        auto kern = k_count_cta<PV, COL, false>;
+        if (smem > 48 * 1024) KC_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        Ctx c = base;
+        c.q0 = q0;
+        c.q1 = q1;
+        c.cursor = cursors + ci++;
+        const int grid = (int)std::min<int64_t>(q1 - q0, (int64_t)sms * blocks_per_sm(kern, NW * 32, smem));
+        kern<<<grid, NW * 32, smem, s>>>(c, W, levels, nullptr, 0);
+        KC_CK(cudaGetLastError());
+    }
+    // W = 1: one warp per owner
+    {
+        const int64_t q0 = ge_at(33), q1 = ge_at(std::max<int64_t>(1, dmin));
+        if (q1 > q0) {
+            Ctx c = base;
+            c.q0 = q0;
+            c.q1 = q1;
+            c.cursor = cursors + ci++;
+            auto kern = k_count_w1<PV, COL>;
+            const int64_t warps = q1 - q0;
+            const int grid = (int)std::min<int64_t>((warps + 7) / 8, (int64_t)sms * blocks_per_sm(kern, 256, 0));
+            kern<<<grid, 256, 0, s>>>(c);
+            KC_CK(cudaGetLastError());
+        }
+    }
+    return KC_OK;
+}
+
+}  // namespace
+
+int64_t heavy_scratch_words(const kc_graph* g, int k, int* slots_out)
+{
+    *slots_out = 0;
+    const int64_t cut = 32LL * smem_max_words();
+    if (g->max_dplus <= cut || k - 1 > g->max_dplus) return 0;
+    const int64_t nheavy = g->ge[(size_t)std::max<int64_t>(cut + 1, k - 1)];
+    if (nheavy <= 0) return 0;
+    const int W = (g->max_dplus + 31) / 32;
+    const int levels = k > 3 ? k - 3 : 1;
+    const Layout lay = make_layout(W, W, 8, levels, true, true);
+    const int64_t slots = std::min<int64_t>(nheavy, num_sms());
+    *slots_out = (int)slots;
+    return lay.total * slots;
+}
+
+kc_status count_launch(const kc_graph* g, const CountArgs& a, unsigned long long* cursors,
+                       uint32_t* heavy_scratch, int64_t heavy_words, cudaStream_t s)
+{
+    Ctx c;
+    c.offp = g->offp;
+    c.adjp = g->adjp;
+    c.queue = g->queue;
+    c.perm = g->perm;
+    c.q0 = c.q1 = 0;
+    c.k = a.k;
+    c.colours = a.colours;
+    c.seed = a.seed;
+    c.total = a.total;
+    c.pv = a.pv;
+    c.po = a.po;
+    c.cursor = nullptr;
+    const bool col = a.colours >= 2;  // one colour keeps every pair
+    if (a.per_vertex) {
+        if (col) return KC_ENOTSUP;
+        return launch_classes<true, false>(g, c, cursors, heavy_scratch, heavy_words, s);
+    }
+    if (col) return launch_classes<false, true>(g, c, cursors, heavy_scratch, heavy_words, s);
+    return launch_classes<false, false>(g, c, cursors, heavy_scratch, heavy_words, s);
+}
+
+}  // namespace kc

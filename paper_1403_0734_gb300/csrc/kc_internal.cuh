@@ -1,0 +1,107 @@
+// kc_internal.cuh -- internal declarations of libkc (not part of the ABI).
+#pragma once
+
+#include <cstdint>
+#include <cstddef>
+#include <vector>
+#include <cuda_runtime.h>
+
+#include "../../include/kc.h"
+
+namespace kc {
+
+// ---------------------------------------------------------------- errors
+
+void set_cuda_error(cudaError_t e, const char* what);
+
+#define KC_CK(call)                                                   \
+    do {                                                              \
+        cudaError_t kc_e_ = (call);                                   \
+        if (kc_e_ != cudaSuccess) {                                   \
+            ::kc::set_cuda_error(kc_e_, #call);                       \
+            return kc_e_ == cudaErrorMemoryAllocation ? KC_ENOMEM     \
+                                                      : KC_ECUDA;     \
+        }                                                             \
+    } while (0)
+
+#define KC_TRY(expr)                                                  \
+    do {                                                              \
+        kc_status kc_s_ = (expr);                                     \
+        if (kc_s_ != KC_OK) return kc_s_;                             \
+    } while (0)
+
+// ------------------------------------------------------------ constants
+
+constexpr int kWarp = 32;
+constexpr uint32_t kFull = 0xffffffffu;
+
+// Owner classes by |Gamma+(u)|: rows of W 32-bit words hold a bitmap row of
+// G+(u).  Class c covers d+ in (32*W(c-1), 32*W(c)].
+constexpr int kNumSmemClasses = 6;               // W = 1, 2, 4, 8, 16, 32
+constexpr int kClassWords[kNumSmemClasses] = {1, 2, 4, 8, 16, 32};
+constexpr int kSmemMaxD = 32 * 32;               // 1024: larger owners use global tiles
+
+// ---------------------------------------------------------- graph handle
+
+}  // namespace kc
+
+struct kc_graph {
+    int device = 0;
+    int32_t n = 0;
+    int64_t m = 0;
+    int32_t max_dplus = 0;
+    int64_t wedges = 0;
+    int32_t* rank = nullptr;   // [n]  vertex id -> rank in the order
+    int32_t* perm = nullptr;   // [n]  rank -> vertex id
+    int32_t* deg = nullptr;    // [n]  degree, rank space
+    int32_t* dplus = nullptr;  // [n]  |Gamma+|, rank space
+    int64_t* offp = nullptr;   // [n+1] oriented CSR offsets, rank space
+    int32_t* adjp = nullptr;   // [m]  oriented CSR columns (ranks), rows ascending
+    int32_t* queue = nullptr;  // [n]  ranks by d+ descending, ties by rank
+    std::vector<int64_t> ge;   // host: ge[t] = #{u : d+(u) >= t}, t = 0..max_dplus+1
+    int64_t bytes = 0;
+};
+
+namespace kc {
+
+// ------------------------------------------------------------ primitives
+
+// Exclusive scan of int32 values into int64 offsets: out[0] = 0,
+// out[i+1] = out[i] + in[i]; out has n+1 entries.  `tmp` must hold
+// scan_tmp_elems(n) int64 values.
+size_t scan_tmp_elems(int64_t n);
+kc_status scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, int64_t* tmp,
+                          cudaStream_t s);
+
+// Stable LSD radix sort of (key, value) pairs by the low `bits` bits of the
+// 32-bit keys.  Buffers are ping-ponged; the sorted result is returned in
+// (*keys, *vals) which point to either the input or the alternate buffers.
+// `hist` must hold radix_hist_elems(n) int32 values, `tmp` scan_tmp_elems of
+// that many values.
+int64_t radix_hist_elems(int64_t n);
+kc_status radix_sort_pairs(uint32_t** keys, int32_t** vals, uint32_t* keys_alt,
+                           int32_t* vals_alt, int64_t n, int bits, int32_t* hist,
+                           int64_t* hist_scan, int64_t* tmp, cudaStream_t s);
+
+// ------------------------------------------------------------ counting
+
+struct CountArgs {
+    int k;
+    uint32_t colours;       // 0: exact FFF_k; >= 1: cFFF_k
+    uint64_t seed;
+    bool per_vertex;        // accumulate memberships into pv (rank space)
+    unsigned long long* total;  // [2] 128-bit total (lo, hi)
+    unsigned long long* pv;     // [n] rank space, nullable
+    unsigned long long* po;     // [n] rank space, nullable
+};
+
+kc_status count_launch(const kc_graph* g, const CountArgs& a, unsigned long long* cursors,
+                       uint32_t* heavy_scratch, int64_t heavy_words, cudaStream_t s);
+
+int smem_max_words();
+kc_status set_smem_max_words(int64_t v);
+
+// Words of global scratch the heavy (global-bitmap) class needs.
+int64_t heavy_scratch_words(const kc_graph* g, int k, int* slots_out);
+
+}  // namespace kc

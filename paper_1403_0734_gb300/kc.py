@@ -1,0 +1,262 @@
+"""Thin ctypes binding of libkc (include/kc.h).
+
+Argument marshalling only: every step of the counting path runs in the CUDA
+kernels behind the C ABI.  Host inputs are numpy arrays; device inputs are
+torch CUDA tensors (PyTorch is used for device memory and streams only).
+The binding refuses to run without the compiled library -- there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libkc.so")
+
+KC_OK, KC_EINVAL, KC_ENOMEM, KC_EOVERFLOW, KC_ETIMEOUT, KC_ECUDA, KC_ENOTSUP = range(7)
+KC_DEVICE_PTRS = 0x1
+KC_VALIDATE = 0x2
+KC_MAX_K = 32
+KC_PARAM_SMEM_MAX_WORDS = 1
+
+_P = ctypes.c_void_p
+_lib = None
+
+
+class KcError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        lib = _load()
+        msg = lib.kc_strerror(status).decode()
+        if status == KC_ECUDA:
+            msg += ": " + lib.kc_last_cuda_error().decode()
+        super().__init__(f"{what}: {msg}")
+        self.status = status
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("m", ctypes.c_int64), ("max_dplus", ctypes.c_int32),
+                ("wedges", ctypes.c_int64), ("device_bytes", ctypes.c_int64)]
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with "
+                          "`python -c 'import __graft_entry__ as g; g.build()'` (needs nvcc)")
+    lib = ctypes.CDLL(LIB_PATH)
+    st = ctypes.c_int
+    lib.kc_strerror.argtypes = [ctypes.c_int]
+    lib.kc_strerror.restype = ctypes.c_char_p
+    lib.kc_last_cuda_error.argtypes = []
+    lib.kc_last_cuda_error.restype = ctypes.c_char_p
+    lib.kc_version.argtypes = []
+    lib.kc_version.restype = ctypes.c_char_p
+    lib.kc_build_csr.argtypes = [ctypes.c_int32, _P, _P, ctypes.c_int64, _P, _P, _P]
+    lib.kc_build_csr.restype = st
+    lib.kc_orient.argtypes = [_P, _P, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint, _P, ctypes.POINTER(_P)]
+    lib.kc_orient.restype = st
+    lib.kc_free.argtypes = [_P]
+    lib.kc_free.restype = None
+    lib.kc_info.argtypes = [_P, ctypes.POINTER(_Info)]
+    lib.kc_info.restype = st
+    lib.kc_export.argtypes = [_P, ctypes.c_uint, _P, _P, _P, _P, _P, _P]
+    lib.kc_export.restype = st
+    lib.kc_count.argtypes = [_P, ctypes.c_int, ctypes.c_uint, _P, _P, _P, _P]
+    lib.kc_count.restype = st
+    lib.kc_estimate.argtypes = [_P, ctypes.c_int, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint, _P, _P, _P, _P]
+    lib.kc_estimate.restype = st
+    lib.kc_count_csr.argtypes = [_P, _P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int, ctypes.c_uint, _P, _P, _P, _P]
+    lib.kc_count_csr.restype = st
+    lib.kc_estimate_csr.argtypes = [_P, _P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int, ctypes.c_uint32,
+                                    ctypes.c_uint64, ctypes.c_uint, _P, _P, _P]
+    lib.kc_estimate_csr.restype = st
+    lib.kc_set_param.argtypes = [ctypes.c_int, ctypes.c_int64]
+    lib.kc_set_param.restype = st
+    lib.kc_get_param.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int64)]
+    lib.kc_get_param.restype = st
+    _lib = lib
+    return lib
+
+
+def _check(status: int, what: str):
+    if status != KC_OK:
+        raise KcError(status, what)
+
+
+def _stream_handle(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available() and torch.cuda.is_initialized():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        return 0
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream  # torch.cuda.Stream
+
+
+def _is_device(a) -> bool:
+    return hasattr(a, "is_cuda") and a.is_cuda
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if _is_device(a):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+def set_param(param: int, value: int):
+    _check(_load().kc_set_param(param, value), "kc_set_param")
+
+
+def get_param(param: int) -> int:
+    v = ctypes.c_int64(0)
+    _check(_load().kc_get_param(param, ctypes.byref(v)), "kc_get_param")
+    return int(v.value)
+
+
+def version() -> str:
+    return _load().kc_version().decode()
+
+
+def build_csr(n: int, src, dst):
+    """Canonical CSR (symmetric, simple, sorted rows) from an edge list (host)."""
+    src = np.ascontiguousarray(src, dtype=np.int32)
+    dst = np.ascontiguousarray(dst, dtype=np.int32)
+    ne = int(src.shape[0])
+    off = np.zeros(n + 1, dtype=np.int64)
+    adj = np.empty(max(2 * ne, 1), dtype=np.int32)
+    m = ctypes.c_int64(0)
+    _check(_load().kc_build_csr(n, src.ctypes.data if ne else None, dst.ctypes.data if ne else None, ne,
+                                off.ctypes.data, adj.ctypes.data, ctypes.byref(m)), "kc_build_csr")
+    return off, adj[: 2 * m.value].copy(), int(m.value)
+
+
+class Graph:
+    """An oriented graph resident on the device (owns a kc_graph handle)."""
+
+    def __init__(self, handle: int):
+        self._h = handle
+        info = _Info()
+        _check(_load().kc_info(handle, ctypes.byref(info)), "kc_info")
+        self.n = int(info.n)
+        self.m = int(info.m)
+        self.max_dplus = int(info.max_dplus)
+        self.wedges = int(info.wedges)
+        self.device_bytes = int(info.device_bytes)
+
+    @property
+    def handle(self) -> int:
+        if not self._h:
+            raise ValueError("graph already freed")
+        return self._h
+
+    def free(self):
+        if self._h:
+            _load().kc_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def orient(off, adj, n: int | None = None, m: int | None = None, validate: bool = False, stream=None) -> Graph:
+    """Round 1: degrees, (degree, id) order and Gamma+ lists on the device.
+    off/adj are numpy arrays (host) or torch CUDA tensors (device)."""
+    dev = _is_device(off)
+    n = int(off.shape[0] - 1) if n is None else n
+    m = int(adj.shape[0] // 2) if m is None else m
+    if not dev:
+        off = np.ascontiguousarray(off, dtype=np.int64)
+        adj = np.ascontiguousarray(adj, dtype=np.int32)
+    flags = (KC_DEVICE_PTRS if dev else 0) | (KC_VALIDATE if validate else 0)
+    h = _P()
+    _check(_load().kc_orient(_ptr(off), _ptr(adj) if m > 0 else None, n, m, flags,
+                             _stream_handle(stream), ctypes.byref(h)), "kc_orient")
+    return Graph(h.value)
+
+
+def export(g: Graph, stream=None) -> dict:
+    """Copy the oriented graph to the host: rank, perm, off_plus, adj_plus, queue."""
+    n, m = g.n, g.m
+    out = {"rank": np.empty(max(n, 1), np.int32), "perm": np.empty(max(n, 1), np.int32),
+           "off_plus": np.empty(n + 1, np.int64), "adj_plus": np.empty(max(m, 1), np.int32),
+           "queue": np.empty(max(n, 1), np.int32)}
+    _check(_load().kc_export(g.handle, 0, out["rank"].ctypes.data, out["perm"].ctypes.data,
+                             out["off_plus"].ctypes.data, out["adj_plus"].ctypes.data,
+                             out["queue"].ctypes.data, _stream_handle(stream)), "kc_export")
+    return {"rank": out["rank"][:n], "perm": out["perm"][:n], "off_plus": out["off_plus"],
+            "adj_plus": out["adj_plus"][:m], "queue": out["queue"][:n]}
+
+
+def count(g: Graph, k: int, per_vertex: bool = False, per_owner: bool = False, stream=None):
+    """FFF_k on the device.  Returns (q_k, per_vertex or None, per_owner or None)
+    with host numpy uint64 arrays indexed by the caller's vertex ids."""
+    pv = np.empty(max(g.n, 1), np.uint64) if per_vertex else None
+    po = np.empty(max(g.n, 1), np.uint64) if per_owner else None
+    tot = ctypes.c_uint64(0)
+    _check(_load().kc_count(g.handle, k, 0, ctypes.byref(tot), _ptr(pv), _ptr(po), _stream_handle(stream)),
+           f"kc_count(k={k})")
+    return int(tot.value), (pv[: g.n] if pv is not None else None), (po[: g.n] if po is not None else None)
+
+
+def count_device(g: Graph, k: int, total, per_vertex=None, per_owner=None, stream=None):
+    """Asynchronous FFF_k into device tensors: total (2 x int64: lo, hi words of
+    the uint64 count, hi != 0 means overflow), per_vertex/per_owner (n x int64,
+    read as uint64)."""
+    _check(_load().kc_count(g.handle, k, KC_DEVICE_PTRS, _ptr(total), _ptr(per_vertex), _ptr(per_owner),
+                            _stream_handle(stream)), f"kc_count(k={k})")
+
+
+def estimate(g: Graph, k: int, colours: int, seed: int, per_owner: bool = False, stream=None):
+    """cFFF_k on the device.  Returns (sampled S, estimate S*c^(k-2), per_owner or None)."""
+    po = np.empty(max(g.n, 1), np.uint64) if per_owner else None
+    s = ctypes.c_uint64(0)
+    est = ctypes.c_double(0.0)
+    _check(_load().kc_estimate(g.handle, k, colours, seed, 0, ctypes.byref(s), ctypes.byref(est), _ptr(po),
+                               _stream_handle(stream)), f"kc_estimate(k={k}, c={colours})")
+    return int(s.value), float(est.value), (po[: g.n] if po is not None else None)
+
+
+def count_csr(off, adj, k: int, per_vertex: bool = False, per_owner: bool = False, validate: bool = False,
+              stream=None):
+    """One-shot FFF_k on a host CSR (orient, count, free)."""
+    off = np.ascontiguousarray(off, dtype=np.int64)
+    adj = np.ascontiguousarray(adj, dtype=np.int32)
+    n = int(off.shape[0] - 1)
+    m = int(adj.shape[0] // 2)
+    pv = np.empty(max(n, 1), np.uint64) if per_vertex else None
+    po = np.empty(max(n, 1), np.uint64) if per_owner else None
+    tot = ctypes.c_uint64(0)
+    flags = KC_VALIDATE if validate else 0
+    _check(_load().kc_count_csr(off.ctypes.data, adj.ctypes.data if m else None, n, m, k, flags,
+                                ctypes.byref(tot), _ptr(pv), _ptr(po), _stream_handle(stream)),
+           f"kc_count_csr(k={k})")
+    return int(tot.value), (pv[:n] if pv is not None else None), (po[:n] if po is not None else None)
+
+
+def estimate_csr(off, adj, k: int, colours: int, seed: int, validate: bool = False, stream=None):
+    """One-shot cFFF_k on a host CSR.  Returns (sampled, estimate)."""
+    off = np.ascontiguousarray(off, dtype=np.int64)
+    adj = np.ascontiguousarray(adj, dtype=np.int32)
+    n = int(off.shape[0] - 1)
+    m = int(adj.shape[0] // 2)
+    s = ctypes.c_uint64(0)
+    est = ctypes.c_double(0.0)
+    flags = KC_VALIDATE if validate else 0
+    _check(_load().kc_estimate_csr(off.ctypes.data, adj.ctypes.data if m else None, n, m, k, colours, seed, flags,
+                                   ctypes.byref(s), ctypes.byref(est), _stream_handle(stream)),
+           f"kc_estimate_csr(k={k})")
+    return int(s.value), float(est.value)

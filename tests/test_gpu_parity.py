@@ -1,0 +1,290 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Integer results are compared bit for bit (totals, per-vertex membership
+counts, per-owner counts, cFFF sampled counts); the cFFF estimate is compared
+exactly too, since both sides round S * c^(k-2) the same way.  Graphs are
+seeded and synthetic; sizes are chosen so the oracle finishes in seconds
+while every owner class (bitmap width 1..32 words and the global-tile path)
+is exercised, with ragged last words.
+"""
+from math import comb
+
+import numpy as np
+import pytest
+
+import kcgen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def kc():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1403_0734_gb300.build as kb
+    kb.build()
+    import paper_1403_0734_gb300 as kc
+    kc.set_param(kc.KC_PARAM_SMEM_MAX_WORDS, 32)
+    yield kc
+    kc.set_param(kc.KC_PARAM_SMEM_MAX_WORDS, 32)
+
+
+def elem_sym(values, k):
+    e = [1] + [0] * k
+    for a in values:
+        for j in range(k, 0, -1):
+            e[j] += e[j - 1] * a
+    return e[k]
+
+
+GRAPHS = {
+    "er_1000": lambda: kcgen.er_1000(),
+    "chunglu_20k": lambda: kcgen.chung_lu(20000, 200000, 2.1, 2000.0, 1),
+    "sbm_20k": lambda: kcgen.sbm(20000, 50, 0.3, 500000, 1),
+    "rmat_s12": lambda: kcgen.rmat(12, 16, 0.57, 0.19, 0.19, 1),
+    "rmat_s14": lambda: kcgen.rmat(14, 16, 0.57, 0.19, 0.19, 1),
+    "chunglu_50k": lambda: kcgen.chung_lu(50000, 1000000, 2.1, 5000.0, 1),
+}
+_cache = {}
+
+
+def graph(name):
+    if name not in _cache:
+        _cache[name] = GRAPHS[name]()
+    return _cache[name]
+
+
+def check_count(kc, g, G, k):
+    total, pv, po = kc.count(G, k, per_vertex=True, per_owner=True)
+    ot, opo, opv = oracle.count(g, k, per_owner=True, per_vertex=True)
+    assert total == ot, (g.name, k, total, ot)
+    assert np.array_equal(po, opo), (g.name, k)
+    assert np.array_equal(pv, opv), (g.name, k)
+    # the total without per-vertex work takes another kernel variant
+    t2, _, _ = kc.count(G, k)
+    assert t2 == ot
+
+
+# ------------------------------------------------------------ orientation
+
+@pytest.mark.parametrize("name", ["er_1000", "chunglu_20k", "sbm_20k", "rmat_s12"])
+def test_orientation_matches_oracle(kc, name):
+    g = graph(name)
+    G = kc.orient(g.off, g.adj, validate=True)
+    ex = kc.export(G)
+    perm, rank, offp, adjp = oracle.oriented(g)
+    assert np.array_equal(ex["perm"], perm)
+    assert np.array_equal(ex["rank"], rank)
+    assert np.array_equal(ex["off_plus"], offp)
+    assert np.array_equal(ex["adj_plus"], adjp)
+    dplus = np.diff(offp)
+    exp_queue = np.lexsort((np.arange(g.n), -dplus))
+    assert np.array_equal(ex["queue"], exp_queue)
+    assert G.max_dplus == int(dplus.max())
+    assert G.wedges == int((dplus * (dplus - 1) // 2).sum())
+    assert G.m == g.m
+
+
+def test_orientation_long_rows(kc):
+    # complete graph: rows of every length 0..n-1, all through the block and
+    # warp fill kernels; equal degrees, so the order is by id
+    g = kcgen.complete(300)
+    G = kc.orient(g.off, g.adj)
+    ex = kc.export(G)
+    assert np.array_equal(ex["perm"], np.arange(300))
+    for r in (0, 1, 150, 298, 299):
+        assert np.array_equal(ex["adj_plus"][ex["off_plus"][r]:ex["off_plus"][r + 1]], np.arange(r + 1, 300))
+
+
+# ------------------------------------------------------------ exact counts
+
+@pytest.mark.parametrize("name,ks", [("er_1000", (3, 4, 5)), ("chunglu_20k", (3, 4, 5, 6, 7)),
+                                     ("sbm_20k", (3, 4, 5, 6, 7)), ("rmat_s12", (3, 4, 5, 6)),
+                                     ("rmat_s14", (3, 4, 5)), ("chunglu_50k", (3, 4))])
+def test_counts_match_oracle(kc, name, ks):
+    g = graph(name)
+    G = kc.orient(g.off, g.adj)
+    for k in ks:
+        check_count(kc, g, G, k)
+
+
+@pytest.mark.parametrize("maxw", [1, 2, 4])
+def test_global_tile_path_matches_oracle(kc, maxw):
+    """Owners wider than `maxw` words are forced onto the global-memory tiles."""
+    kc.set_param(kc.KC_PARAM_SMEM_MAX_WORDS, maxw)
+    try:
+        for name, ks in (("rmat_s14", (3, 4, 5)), ("chunglu_20k", (3, 4, 6))):
+            g = graph(name)
+            G = kc.orient(g.off, g.adj)
+            for k in ks:
+                check_count(kc, g, G, k)
+    finally:
+        kc.set_param(kc.KC_PARAM_SMEM_MAX_WORDS, 32)
+
+
+def test_wide_dense_owners_match_oracle(kc):
+    # G(n, p) dense: owners with |Gamma+| in the 8-, 16- and 32-word classes
+    for n, p, seed, ks in ((700, 0.45, 1, (3, 4)), (1400, 0.5, 2, (3,))):
+        g = kcgen.random_small(n, p, seed)
+        G = kc.orient(g.off, g.adj)
+        assert G.max_dplus > 256
+        for k in ks:
+            check_count(kc, g, G, k)
+
+
+@pytest.mark.parametrize("n,ks", [(31, (3, 5, 8, 31, 32)), (33, (3, 4, 7, 33)), (64, (3, 4, 6)),
+                                  (65, (3, 5)), (200, (3, 4, 5, 7)), (520, (3, 4)), (1100, (3, 4)),
+                                  (1500, (3,))])
+def test_complete_graph_closed_form(kc, n, ks):
+    g = kcgen.complete(n)
+    G = kc.orient(g.off, g.adj)
+    for k in ks:
+        total, pv, po = kc.count(G, k, per_vertex=True, per_owner=True)
+        assert total == comb(n, k)
+        assert np.all(pv == comb(n - 1, k - 1))
+        assert [int(x) for x in po] == [comb(n - 1 - r, k - 1) for r in range(n)]
+
+
+@pytest.mark.parametrize("parts,ks", [((10,) * 60, (3, 4, 5)), ((7, 9, 11, 13) * 12, (3, 4, 6)),
+                                      ((3,) * 400, (3, 4))])
+def test_complete_multipartite_closed_form(kc, parts, ks):
+    g = kcgen.complete_multipartite(parts, shuffle_seed=5)
+    label = np.repeat(np.arange(len(parts)), parts)[np.random.default_rng(5).permutation(sum(parts))]
+    G = kc.orient(g.off, g.adj)
+    for k in ks:
+        total, pv, _ = kc.count(G, k, per_vertex=True)
+        assert total == elem_sym(parts, k)
+        for v in range(0, g.n, 17):
+            rest = [a for i, a in enumerate(parts) if i != label[v]]
+            assert int(pv[v]) == elem_sym(rest, k - 1)
+
+
+def test_uint64_scale_counts(kc):
+    # C(200, 7) ~ 2.3e12 and C(120, 10) ~ 1.2e14: counts far above 2^32
+    for n, k in ((200, 7), (120, 10)):
+        g = kcgen.complete(n)
+        G = kc.orient(g.off, g.adj)
+        assert kc.count(G, k)[0] == comb(n, k)
+
+
+# ------------------------------------------------------------ cFFF_k
+
+@pytest.mark.parametrize("name", ["chunglu_20k", "sbm_20k", "rmat_s12"])
+def test_estimate_matches_oracle(kc, name):
+    g = graph(name)
+    G = kc.orient(g.off, g.adj)
+    for k in (3, 4, 5, 6):
+        for c, seed in ((2, 1), (3, 7), (4, 1), (8, 2), (16, 3)):
+            s, est, po = kc.estimate(G, k, c, seed, per_owner=True)
+            os_, oest, opo = oracle.estimate(g, k, c, seed, per_owner=True)
+            assert s == os_, (name, k, c, seed, s, os_)
+            assert est == oest
+            assert np.array_equal(po, opo)
+
+
+def test_estimate_one_colour_is_exact(kc):
+    g = graph("chunglu_20k")
+    G = kc.orient(g.off, g.adj)
+    for k in (3, 5):
+        s, est, _ = kc.estimate(G, k, 1, 99)
+        assert s == kc.count(G, k)[0] and est == float(s)
+
+
+def test_estimate_global_tiles(kc):
+    kc.set_param(kc.KC_PARAM_SMEM_MAX_WORDS, 1)
+    try:
+        g = graph("rmat_s14")
+        G = kc.orient(g.off, g.adj)
+        for k, c in ((3, 2), (4, 3), (5, 2)):
+            assert kc.estimate(G, k, c, 5)[0] == oracle.estimate(g, k, c, 5)[0]
+    finally:
+        kc.set_param(kc.KC_PARAM_SMEM_MAX_WORDS, 32)
+
+
+# ------------------------------------------------------------ edge cases
+
+def test_edge_cases(kc):
+    # isolated vertices only
+    g = kcgen.empty(10)
+    G = kc.orient(g.off, g.adj)
+    assert kc.count(G, 1)[0] == 10 and kc.count(G, 2)[0] == 0 and kc.count(G, 3)[0] == 0
+    # no vertices at all
+    G = kc.orient(np.zeros(1, np.int64), np.zeros(0, np.int32))
+    assert kc.count(G, 3)[0] == 0 and kc.count(G, 1)[0] == 0
+    # k above the clique number, k = 1 and 2 with per-vertex outputs
+    g = graph("er_1000")
+    G = kc.orient(g.off, g.adj)
+    assert kc.count(G, 6)[0] == 0
+    t, pv, po = kc.count(G, 1, per_vertex=True, per_owner=True)
+    assert t == g.n and np.all(pv == 1) and np.all(po == 1)
+    t, pv, po = kc.count(G, 2, per_vertex=True, per_owner=True)
+    assert t == g.m and np.array_equal(pv, g.degrees().astype(np.uint64))
+    assert np.array_equal(po, oracle.count(g, 2, per_owner=True)[1])
+    # invalid k
+    for k in (0, -1, 33):
+        with pytest.raises(kc.KcError):
+            kc.count(G, k)
+    with pytest.raises(kc.KcError):
+        kc.estimate(G, 3, 0, 1)
+
+
+def test_validate_rejects_malformed(kc):
+    g = kcgen.cycle(6)
+    bad = g.adj.copy()
+    bad[0], bad[1] = bad[1], bad[0]  # unsorted row
+    with pytest.raises(kc.KcError):
+        kc.orient(g.off, bad, validate=True)
+    asym = kcgen.from_edges(4, [(0, 1), (1, 2), (2, 3)])
+    a = asym.adj.copy()
+    a[-1] = 0  # row 3 now says (3, 0) without (0, 3)
+    with pytest.raises(kc.KcError):
+        kc.orient(asym.off, a, validate=True)
+
+
+def test_cycle_tie_break_and_small_graphs(kc):
+    for g in (kcgen.cycle(3), kcgen.cycle(10), kcgen.star(40), kcgen.path(5)):
+        G = kc.orient(g.off, g.adj, validate=True)
+        for k in (2, 3, 4):
+            check_count(kc, g, G, k)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_random_small_graphs(kc, seed):
+    g = kcgen.random_small(40 + 7 * seed, 0.35 + 0.08 * seed, 100 + seed)
+    G = kc.orient(g.off, g.adj, validate=True)
+    for k in range(3, 9):
+        check_count(kc, g, G, k)
+
+
+# ------------------------------------------------------------ API forms
+
+def test_one_shot_and_device_pointer_forms(kc):
+    import torch
+    g = graph("rmat_s12")
+    ot, opo, opv = oracle.count(g, 4, per_owner=True, per_vertex=True)
+    t, pv, po = kc.count_csr(g.off, g.adj, 4, per_vertex=True, per_owner=True, validate=True)
+    assert t == ot and np.array_equal(pv, opv) and np.array_equal(po, opo)
+    s, est = kc.estimate_csr(g.off, g.adj, 4, 3, 7)
+    assert (s, est) == oracle.estimate(g, 4, 3, 7)[:2]
+    # inputs and outputs resident on the device
+    off = torch.from_numpy(g.off).cuda()
+    adj = torch.from_numpy(g.adj).cuda()
+    G = kc.orient(off, adj)
+    total = torch.zeros(2, dtype=torch.int64, device="cuda")
+    dpv = torch.zeros(g.n, dtype=torch.int64, device="cuda")
+    dpo = torch.zeros(g.n, dtype=torch.int64, device="cuda")
+    kc.count_device(G, 4, total, dpv, dpo)
+    torch.cuda.synchronize()
+    assert int(total[0]) == ot and int(total[1]) == 0
+    assert np.array_equal(dpv.cpu().numpy().view(np.uint64), opv)
+    assert np.array_equal(dpo.cpu().numpy().view(np.uint64), opo)
+
+
+def test_repeatable(kc):
+    g = graph("chunglu_20k")
+    G = kc.orient(g.off, g.adj)
+    a = kc.count(G, 5, per_vertex=True)
+    b = kc.count(G, 5, per_vertex=True)
+    assert a[0] == b[0] and np.array_equal(a[1], b[1])
