@@ -134,7 +134,7 @@ def test_wide_dense_owners_match_oracle(kc):
             check_count(kc, g, G, k)
 
 
-@pytest.mark.parametrize("n,ks", [(31, (3, 5, 8, 31, 32)), (33, (3, 4, 7, 33)), (64, (3, 4, 6)),
+@pytest.mark.parametrize("n,ks", [(31, (3, 5, 8, 31, 32)), (33, (3, 4, 7, 32)), (64, (3, 4, 6)),
                                   (65, (3, 5)), (200, (3, 4, 5, 7)), (520, (3, 4)), (1100, (3, 4)),
                                   (1500, (3,))])
 def test_complete_graph_closed_form(kc, n, ks):
@@ -162,11 +162,15 @@ def test_complete_multipartite_closed_form(kc, parts, ks):
 
 
 def test_uint64_scale_counts(kc):
-    # C(200, 7) ~ 2.3e12 and C(120, 10) ~ 1.2e14: counts far above 2^32
-    for n, k in ((200, 7), (120, 10)):
-        g = kcgen.complete(n)
+    # counts far above 2^32 with little search work: the last two levels are
+    # closed by popcounts, so K_{600,600,600,600} (k = 4) has 600^4 ~ 1.3e11
+    # cliques but only ~2e6 search nodes; K_{2000,2000,2000} (k = 3) has 8e9
+    for parts, k in (((600,) * 4, 4), ((2000,) * 3, 3)):
+        g = kcgen.complete_multipartite(parts, shuffle_seed=1)
         G = kc.orient(g.off, g.adj)
-        assert kc.count(G, k)[0] == comb(n, k)
+        total, pv, _ = kc.count(G, k, per_vertex=True)
+        assert total == elem_sym(parts, k) and total > 2**32
+        assert int(pv.sum()) == k * total
 
 
 # ------------------------------------------------------------ cFFF_k
