@@ -1,0 +1,369 @@
+#!/usr/bin/env python
+"""bench.py -- k-clique counting throughput (FFF_k) on GB300.
+
+One step = the whole hot path once over the Chung-Lu power-law workload
+(n = 10^6, 2*10^7 endpoint draws, exponent 2.1, max weight 20000, seed 1):
+orientation (degrees, (degree, id) order, Gamma+ lists, owner queue) from a
+device-resident CSR, then exact counts for k = 3, 4, 5, 6 with per-vertex and
+per-owner outputs written to device buffers.  value = cliques counted per
+second (sum over k of q_k / step time).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl kc|reference]
+
+Under torchrun every rank counts its own graph (seed 1 + rank: weak
+scaling); rank 0 prints one JSON line.  --impl reference times the CPU
+oracle on the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import glob
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "k-cliques/sec and edges/sec at k=3..7 on 1 GB300; % HBM roofline; batched p50/p99"
+UNIT = "k-cliques/s"
+WORKLOAD = "chung_lu n=1e6 m~2e7 gamma=2.1 wmax=20000 seed=1+rank, exact k=3..6, per-vertex+per-owner"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "roofline_traffic.json")
+# Word-operation peak of the counting kernels: one 32-bit AND, population
+# count and add per word; the population count issues at 16 lanes per clock
+# per SM, so the peak is 16 x 152 SMs x clock (derivation in the design doc).
+POPC_LANES_PER_SM_CLK = 16
+NUM_SMS = 152
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["kc", "reference"], default="kc")
+    ap.add_argument("--ks", default="3,4,5,6")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0,
+                    help="CPU budget of the oracle sample (all k together)")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ helpers
+
+def sources_sha():
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_1403_0734_gb300", "csrc", "*"))):
+        with open(p, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.path = tempfile.mktemp(prefix="kc_clocks_", suffix=".csv")
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) >= 9:
+                    rows.append(p)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ------------------------------------------------------------------ CPU side
+
+def oracle_sample(g, ks, budget_s: float, nthreads: int = 0):
+    """Oracle (as it stands) over owners in id order, chunk by chunk, until the
+    budget is spent; ids are a seeded shuffle of weight order, so a prefix of
+    ids is a uniform sample of owners.  Returns (cliques, seconds, owners)."""
+    import oracle
+    cliques, secs, owners = 0, 0.0, 0
+    per_k = budget_s / len(ks)
+    for k in ks:
+        t_k, lo, chunk = 0.0, 0, 64
+        while t_k < per_k and lo < g.n:
+            hi = min(g.n, lo + chunk)
+            t0 = time.perf_counter()
+            q = oracle.count(g, k, u_range=(lo, hi), nthreads=nthreads)[0]
+            dt = time.perf_counter() - t0
+            cliques += q
+            t_k += dt
+            lo = hi
+            if dt < 0.25 * per_k / 8:
+                chunk = min(chunk * 2, 1 << 16)
+        secs += t_k
+        owners = max(owners, lo)
+    return cliques, secs, owners
+
+
+def cpu_baseline(g, ks, budget_s):
+    import oracle
+    cores = oracle.max_threads(0)
+    q, s, owners = oracle_sample(g, ks, budget_s)
+    return {"value": q / s if s > 0 else None, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"owners with ids 0..{owners - 1} of {g.n} (uniform: ids are shuffled), "
+                      f"k={','.join(map(str, ks))}, {q} cliques in {s:.1f} s on {cores} threads"}
+
+
+def run_reference(args, ks):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import kcgen
+    import oracle
+    g = kcgen.chung_lu_1m(seed=1)
+    cores = oracle.max_threads(0)
+    budget = max(5.0, args.cpu_seconds / max(1, args.steps))
+    for _ in range(args.warmup):
+        oracle_sample(g, ks, min(budget, 3.0))
+    tot_q, tot_s = 0, 0.0
+    owners = 0
+    for _ in range(args.steps):
+        q, s, owners = oracle_sample(g, ks, budget)
+        tot_q += q
+        tot_s += s
+    value = tot_q / tot_s
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": "bounded owner prefix"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"owners with ids 0..{owners - 1} per step, "
+                                       f"{budget:.0f} s of oracle time per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------ GPU side
+
+def main():
+    args = parse()
+    ks = [int(x) for x in args.ks.split(",")]
+    if args.impl == "reference":
+        return run_reference(args, ks)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__
+    import kcgen
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    __graft_entry__.build() if rank == 0 else None
+    if world > 1:
+        dist.barrier()
+    import paper_1403_0734_gb300 as kc
+
+    g = kcgen.chung_lu_1m(seed=1 + rank)
+    off_d = torch.from_numpy(g.off).cuda()
+    adj_d = torch.from_numpy(g.adj).cuda()
+    n = g.n
+    tot = {k: torch.zeros(2, dtype=torch.int64, device="cuda") for k in ks}
+    pv = {k: torch.zeros(n, dtype=torch.int64, device="cuda") for k in ks}
+    po = {k: torch.zeros(n, dtype=torch.int64, device="cuda") for k in ks}
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step(evs=None):
+        if evs:
+            evs[0].record(stream)
+        G = kc.orient(off_d, adj_d)
+        if evs:
+            evs[1].record(stream)
+        for i, k in enumerate(ks):
+            kc.count_device(G, k, tot[k], pv[k], po[k])
+            if evs:
+                evs[2 + i].record(stream)
+        return G
+
+    def sync_all():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+
+    # warm-up
+    for _ in range(args.warmup):
+        G = step()
+        torch.cuda.synchronize()
+        G.free()
+
+    kc.set_param(kc.KC_PARAM_LAUNCH_COUNT, 0)
+    step_ms, orient_ms, k_ms = [], [], {k: [] for k in ks}
+    with Clocks(local) as clk:
+        for _ in range(args.steps):
+            flush.zero_()  # L2 (129 MB) flushed between timed steps
+            sync_all()
+            evs = [torch.cuda.Event(enable_timing=True) for _ in range(2 + len(ks))]
+            G = step(evs)
+            sync_all()
+            step_ms.append(evs[0].elapsed_time(evs[-1]))
+            orient_ms.append(evs[0].elapsed_time(evs[1]))
+            for i, k in enumerate(ks):
+                k_ms[k].append(evs[1 + i].elapsed_time(evs[2 + i]))
+            G.free()
+    launches = kc.get_param(kc.KC_PARAM_LAUNCH_COUNT)
+    clocks = clk.summary()
+
+    q = {k: int(tot[k][0].item()) for k in ks}
+    assert all(int(tot[k][1].item()) == 0 for k in ks), "count overflow"
+    for k in ks:  # invariants the paper fixes: memberships sum to k q_k, owners to q_k
+        assert int(pv[k].sum().item()) == k * q[k] and int(po[k].sum().item()) == q[k]
+    cliques = sum(q.values())
+    ms = statistics.mean(step_ms)
+    t = torch.tensor([ms, float(cliques), float(g.m)], dtype=torch.float64, device="cuda")
+    if world > 1:
+        tmax = t.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        ms_all, cliques_all, m_all = float(tmax[0]), float(t[1]), float(t[2])
+    else:
+        ms_all, cliques_all, m_all = ms, float(cliques), float(g.m)
+
+    # roofline of the dominant call (counting at the largest k), untimed work count
+    kmax = max(ks)
+    kc.set_param(kc.KC_PARAM_WORK_COUNT, 1)
+    G = kc.orient(off_d, adj_d)
+    kc.count(G, kmax, per_vertex=True, per_owner=True)
+    work = kc.get_param(kc.KC_PARAM_WORK_COUNT)
+    kc.set_param(kc.KC_PARAM_WORK_COUNT, 0)
+    kmax_ms = statistics.mean(k_ms[kmax])
+    pk, pk_kind = peaks()
+    clock_mhz = float(pk.get("sm_max_mhz", 2070.0))
+    peak_wops = POPC_LANES_PER_SM_CLK * NUM_SMS * clock_mhz * 1e6 / 1e12  # Tword-op/s
+    achieved = work / (kmax_ms * 1e-3) / 1e12
+    traffic = None
+    try:
+        with open(TRAFFIC_FILE) as f:
+            tr = json.load(f)
+        if tr.get("sources_sha") == sources_sha():
+            traffic = tr.get("dram_bytes_per_launch")
+    except (OSError, ValueError):
+        pass
+    roofline = {"bound": "alu", "kernel": f"kc_count k={kmax} (counting kernels)", "achieved": achieved,
+                "peak": peak_wops, "unit": "Tword-op/s", "frac": achieved / peak_wops, "traffic": traffic,
+                "work_word_ops": work, "peak_kind": f"derived from {pk_kind} max SM clock"}
+    # orientation: HBM-bound streaming (algorithmic bytes ~ 20m + 32n)
+    orient_bytes = 20 * g.m + 32 * g.n
+    om = statistics.mean(orient_ms)
+    orient_roof = {"bound": "hbm", "achieved": orient_bytes / (om * 1e-3) / 1e9,
+                   "peak": float(pk.get("hbm_gbs", 6800.0)), "unit": "GB/s", "algorithmic_bytes": orient_bytes}
+    orient_roof["frac"] = orient_roof["achieved"] / orient_roof["peak"]
+
+    # end to end through the C ABI with host buffers (pinned), one rank's view
+    e2e = None
+    if not args.no_e2e:
+        off_h = torch.from_numpy(g.off).pin_memory().numpy()
+        adj_h = torch.from_numpy(g.adj).pin_memory().numpy()
+        outs = {k: (torch.empty(n, dtype=torch.int64).pin_memory().numpy().view(np.uint64),
+                    torch.empty(n, dtype=torch.int64).pin_memory().numpy().view(np.uint64)) for k in ks}
+
+        def e2e_step():
+            Gh = kc.orient(off_h, adj_h)
+            s = 0
+            for k in ks:
+                s += kc.count(Gh, k, out_pv=outs[k][0], out_po=outs[k][1])[0]
+            Gh.free()
+            return s
+
+        e2e_step()
+        ts = []
+        for _ in range(max(1, min(args.steps, 3))):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s = e2e_step()
+            ts.append(time.perf_counter() - t0)
+            assert s == cliques
+        h2d = g.off.nbytes + g.adj.nbytes
+        d2h = len(ks) * (8 + 2 * 8 * n)
+        e2e = {"value": cliques / statistics.mean(ts), "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * statistics.mean(ts)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(g, ks, args.cpu_seconds)
+
+    if rank == 0:
+        per_k = {str(k): {"q": q[k], "ms": statistics.mean(k_ms[k]),
+                          "cliques_per_s": q[k] / (statistics.mean(k_ms[k]) * 1e-3),
+                          "edges_per_s": g.m / ((statistics.mean(k_ms[k]) + om) * 1e-3)} for k in ks}
+        line = {"metric": METRIC, "value": cliques_all / (ms_all * 1e-3), "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_all, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "n": g.n, "m": g.m, "ks": ks,
+                           "l2": "flushed between timed steps (512 MiB write)",
+                           "parallelism": f"replicas x{world} (one graph per rank)"},
+                "edges_per_s": m_all / (ms_all * 1e-3), "orient_ms": om, "per_k": per_k,
+                "roofline": roofline, "orient_roofline": orient_roof, "clocks": clocks,
+                "gpu_launches": launches, "e2e": e2e, "cpu_baseline": cpu}
+        print(json.dumps(line))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

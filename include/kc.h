@@ -179,9 +179,17 @@ kc_status kc_estimate(const kc_graph* g, int k, uint32_t colours, uint64_t seed,
  *   KC_PARAM_SMEM_MAX_WORDS  owners whose bitmap rows need at most this many
  *       32-bit words (|Gamma+(u)| <= 32 * value) keep G+(u) in shared memory;
  *       wider owners use global-memory tiles.  1..32, default 32.
+ *   KC_PARAM_LAUNCH_COUNT  read: kernels launched by this process so far;
+ *       write 0 to reset.
+ *   KC_PARAM_WORK_COUNT  write 1 (0) to turn on (off) work counting in the
+ *       counting kernels; read: bitmap word-operations (a 32-bit AND plus
+ *       population count) executed by the last synchronous kc_count /
+ *       kc_estimate on this process while counting was on.
  * kc_set_param returns KC_EINVAL for an unknown knob or a value out of range.
  */
 #define KC_PARAM_SMEM_MAX_WORDS 1
+#define KC_PARAM_LAUNCH_COUNT   2
+#define KC_PARAM_WORK_COUNT     3
 kc_status kc_set_param(int param, int64_t value);
 kc_status kc_get_param(int param, int64_t* value);
 

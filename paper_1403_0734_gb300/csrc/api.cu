@@ -1,5 +1,6 @@
 // api.cu -- the extern "C" entry points of libkc (declared in include/kc.h).
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -16,6 +17,13 @@ int num_sms();
 namespace {
 
 thread_local char g_cuda_err[256] = "no error";
+std::atomic<int64_t> g_launches{0};
+}  // namespace
+
+bool g_work_enabled = false;
+unsigned long long g_last_work = 0;
+
+namespace {
 
 // out[perm[r]] = in[r]  (rank space -> caller ids)
 __global__ void k_permute_u64(const unsigned long long* __restrict__ in, const int32_t* __restrict__ perm,
@@ -101,7 +109,7 @@ kc_status run_count(const kc_graph* g, int k, uint32_t colours, uint64_t seed, u
     const bool dev = (flags & KC_DEVICE_PTRS) != 0;
     const int32_t n = g->n;
     Scratch sc(s);
-    unsigned long long* small = nullptr;  // [0..1] total lo/hi, [2..9] cursors
+    unsigned long long* small = nullptr;  // [0..1] total lo/hi, [2..9] cursors, [10] work
     KC_TRY(sc.get(&small, 16));
     KC_CK(cudaMemsetAsync(small, 0, 16 * sizeof(unsigned long long), s));
 
@@ -120,17 +128,17 @@ kc_status run_count(const kc_graph* g, int k, uint32_t colours, uint64_t seed, u
     if (k <= 2) {
         const unsigned long long q = k == 1 ? (unsigned long long)n : (unsigned long long)g->m;
         k_fill_u64<<<1, 32, 0, s>>>(small, 1, q);
-        KC_CK(cudaGetLastError());
+        KC_LAUNCHED();
         if (n > 0) {
             if (out_pv) {
                 if (k == 1) k_fill_u64<<<grid1d(n), 256, 0, s>>>(out_pv, n, 1ull);
                 else k_permute_i32_to_u64<<<grid1d(n), 256, 0, s>>>(g->deg, g->perm, n, out_pv);
-                KC_CK(cudaGetLastError());
+                KC_LAUNCHED();
             }
             if (out_po) {
                 if (k == 1) k_fill_u64<<<grid1d(n), 256, 0, s>>>(out_po, n, 1ull);
                 else k_permute_i32_to_u64<<<grid1d(n), 256, 0, s>>>(g->dplus, g->perm, n, out_po);
-                KC_CK(cudaGetLastError());
+                KC_LAUNCHED();
             }
         }
     } else if (n > 0) {
@@ -156,14 +164,15 @@ kc_status run_count(const kc_graph* g, int k, uint32_t colours, uint64_t seed, u
         a.total = small;
         a.pv = pv_rank;
         a.po = po_rank;
+        a.work = g_work_enabled ? small + 10 : nullptr;
         KC_TRY(count_launch(g, a, small + 2, heavy, hw, s));
         if (pv_rank) {
             k_permute_u64<<<grid1d(n), 256, 0, s>>>(pv_rank, g->perm, n, out_pv);
-            KC_CK(cudaGetLastError());
+            KC_LAUNCHED();
         }
         if (po_rank) {
             k_permute_u64<<<grid1d(n), 256, 0, s>>>(po_rank, g->perm, n, out_po);
-            KC_CK(cudaGetLastError());
+            KC_LAUNCHED();
         }
     }
 
@@ -171,16 +180,21 @@ kc_status run_count(const kc_graph* g, int k, uint32_t colours, uint64_t seed, u
         KC_CK(cudaMemcpyAsync(total, small, 2 * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
         return KC_OK;
     }
-    unsigned long long th[2] = {0, 0};
+    unsigned long long th[11] = {0};
     KC_CK(cudaMemcpyAsync(th, small, sizeof(th), cudaMemcpyDeviceToHost, s));
     KC_TRY(copy_out_u64(per_vertex, out_pv, n, false, s));
     KC_TRY(copy_out_u64(per_owner, out_po, n, false, s));
     KC_CK(cudaStreamSynchronize(s));
     *total = th[0];
+    if (g_work_enabled) g_last_work = th[10];
     return th[1] ? KC_EOVERFLOW : KC_OK;
 }
 
 }  // namespace
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
+void reset_launch_count() { g_launches.store(0, std::memory_order_relaxed); }
 
 void set_cuda_error(cudaError_t e, const char* what)
 {
@@ -314,6 +328,16 @@ kc_status kc_estimate(const kc_graph* g, int k, uint32_t colours, uint64_t seed,
 kc_status kc_set_param(int param, int64_t value)
 {
     if (param == KC_PARAM_SMEM_MAX_WORDS) return kc::set_smem_max_words(value);
+    if (param == KC_PARAM_LAUNCH_COUNT) {
+        if (value != 0) return KC_EINVAL;
+        kc::reset_launch_count();
+        return KC_OK;
+    }
+    if (param == KC_PARAM_WORK_COUNT) {
+        if (value != 0 && value != 1) return KC_EINVAL;
+        kc::g_work_enabled = value != 0;
+        return KC_OK;
+    }
     return KC_EINVAL;
 }
 
@@ -322,6 +346,14 @@ kc_status kc_get_param(int param, int64_t* value)
     if (!value) return KC_EINVAL;
     if (param == KC_PARAM_SMEM_MAX_WORDS) {
         *value = kc::smem_max_words();
+        return KC_OK;
+    }
+    if (param == KC_PARAM_LAUNCH_COUNT) {
+        *value = kc::launch_count();
+        return KC_OK;
+    }
+    if (param == KC_PARAM_WORK_COUNT) {
+        *value = (int64_t)kc::g_last_work;
         return KC_OK;
     }
     return KC_EINVAL;

@@ -58,6 +58,7 @@ struct Ctx {
     unsigned long long* pv;
     unsigned long long* po;
     unsigned long long* cursor;
+    unsigned long long* work;  // nullable: bitmap word-operations executed
 };
 
 // colour(u, x): splitmix64 output function over seed ^ (G * (u<<32 | x)),
@@ -156,10 +157,12 @@ __global__ void __launch_bounds__(256) k_count_w1(Ctx c)
         }
 
         // (c) depth-first search; level t's state of the chain is kept in lane t
-        unsigned long long tot = 0, pvl = 0;
+        unsigned long long tot = 0, pvl = 0, wk = 0;
+        const bool cw = c.work != nullptr;
         const uint32_t C1 = d >= 32 ? kFull : ((1u << d) - 1u);
         if (r0 == 2) {
             tot = leaf2_w1<PV>(C1, up, A, lane, pvl);
+            if (cw) wk += (unsigned long long)__popc(C1) * (PV ? 2 : 1);
         } else {
             uint32_t st_rem = 0;
             int st_e = 0;
@@ -182,8 +185,10 @@ __global__ void __launch_bounds__(256) k_count_w1(Ctx c)
                 cur &= cur - 1u;
                 const uint32_t Cn = cur & __shfl_sync(kFull, up, e);
                 const int need = r0 - t - 1;
+                if (cw) wk += 1;
                 if (__popc(Cn) < need) continue;
                 if (need == 2) {
+                    if (cw) wk += (unsigned long long)__popc(Cn) * (PV ? 2 : 1);
                     const unsigned long long E = leaf2_w1<PV>(Cn, up, A, lane, pvl);
                     tot += E;
                     cur_sub += E;
@@ -204,6 +209,7 @@ __global__ void __launch_bounds__(256) k_count_w1(Ctx c)
             add_total(c.total, tot);
             if (c.po) c.po[r] = tot;
             if (PV && tot) atomicAdd(&c.pv[r], tot);
+            if (cw && wk) atomicAdd(c.work, wk);
         }
         if (PV && lane < d && pvl) atomicAdd(&c.pv[x], pvl);
     }
@@ -251,7 +257,8 @@ __device__ __forceinline__ int warp_and(const uint32_t* a, const uint32_t* b, ui
 // element's degree inside C to pv.
 template <bool PV>
 __device__ unsigned long long warp_leaf2(const uint32_t* C, int low, int W, const uint32_t* A, int RS,
-                                         int32_t* el, unsigned long long* pv, int lane)
+                                         int32_t* el, unsigned long long* pv, int lane,
+                                         unsigned long long* wk)
 {
     int nel = 0, hiw = low;
     const uint32_t lt = mask_below(lane);
@@ -269,7 +276,7 @@ __device__ unsigned long long warp_leaf2(const uint32_t* C, int low, int W, cons
         }
     }
     __syncwarp();
-    unsigned long long E = 0;
+    unsigned long long E = 0, wl = 0;
     for (int p = lane; p < nel; p += 32) {
         const int e = el[p];
         const int we = e >> 5, be = e & 31;
@@ -277,6 +284,7 @@ __device__ unsigned long long warp_leaf2(const uint32_t* C, int low, int W, cons
         uint32_t cnt = (uint32_t)__popc(C[we] & Ae[we] & mask_above(be));
         for (int w = we + 1; w < hiw; ++w) cnt += (uint32_t)__popc(C[w] & Ae[w]);
         E += cnt;
+        if (wk) wl += (unsigned long long)(hiw - we) + (PV ? (unsigned long long)(we - low + 1) : 0ull);
         if (PV) {
             uint32_t lowc = (uint32_t)__popc(C[we] & Ae[we] & mask_below(be));
             for (int w = low; w < we; ++w) lowc += (uint32_t)__popc(C[w] & Ae[w]);
@@ -284,6 +292,7 @@ __device__ unsigned long long warp_leaf2(const uint32_t* C, int low, int W, cons
         }
     }
     __syncwarp();
+    if (wk) *wk += warp_sum64(wl);
     return warp_sum64(E);
 }
 
@@ -294,7 +303,8 @@ __device__ unsigned long long warp_leaf2(const uint32_t* C, int low, int W, cons
 // credits chain members inside it.
 template <bool PV>
 __device__ unsigned long long warp_dfs(uint32_t* stk, int SW, int W, int low0, int need0, const uint32_t* A,
-                                       int RS, int32_t* el, unsigned long long* pv, int lane)
+                                       int RS, int32_t* el, unsigned long long* pv, int lane,
+                                       unsigned long long* wk)
 {
     unsigned long long total = 0, cur_sub = 0, st_sub = 0;
     int t = 0, low = low0, st_low = 0, st_e = 0;
@@ -313,9 +323,10 @@ __device__ unsigned long long warp_dfs(uint32_t* stk, int SW, int W, int low0, i
         const int need = need0 - t - 1;
         const int we = e >> 5;
         const int cnt = warp_and(stk + (int64_t)t * SW, A + (int64_t)e * RS, stk + (int64_t)(t + 1) * SW, we, W, lane);
+        if (wk) *wk += (unsigned long long)(W - we);
         if (cnt < need) continue;
         if (need == 2) {
-            const unsigned long long E = warp_leaf2<PV>(stk + (int64_t)(t + 1) * SW, we, W, A, RS, el, pv, lane);
+            const unsigned long long E = warp_leaf2<PV>(stk + (int64_t)(t + 1) * SW, we, W, A, RS, el, pv, lane, wk);
             total += E;
             cur_sub += E;
             if (PV && lane == 0 && E) atomicAdd(&pv[e], E);
@@ -422,7 +433,8 @@ __global__ void __launch_bounds__(256) k_count_cta(Ctx c, int W, int levels, uin
         __syncthreads();
 
         // (c) count
-        unsigned long long wtot = 0;
+        unsigned long long wtot = 0, wk = 0;
+        unsigned long long* wkp = c.work ? &wk : nullptr;
         if (r0 == 2) {
             for (int e = wid; e < d; e += NW) {
                 const uint32_t* Ae = sA + (int64_t)e * RS;
@@ -436,6 +448,7 @@ __global__ void __launch_bounds__(256) k_count_cta(Ctx c, int W, int levels, uin
                     for (int w = lane; w < Wd; w += 32) all += (unsigned)__popc(Ae[w]);
                 up = __reduce_add_sync(kFull, up);
                 wtot += up;
+                if (wkp) wk += (unsigned long long)(Wd - we) + (PV ? (unsigned long long)Wd : 0ull);
                 if (PV) {
                     all = __reduce_add_sync(kFull, all);
                     if (lane == 0 && all) sPV[e] += all;
@@ -459,15 +472,17 @@ __global__ void __launch_bounds__(256) k_count_cta(Ctx c, int W, int levels, uin
                 }
                 __syncwarp();
                 cnt = (int)__reduce_add_sync(kFull, (unsigned)cnt);
+                if (wkp) wk += (unsigned long long)(Wd - we);
                 if (cnt < need0) continue;
                 const unsigned long long sub =
-                    need0 == 2 ? warp_leaf2<PV>(stk, we, Wd, sA, RS, el, sPV, lane)
-                               : warp_dfs<PV>(stk, W, Wd, we, need0, sA, RS, el, sPV, lane);
+                    need0 == 2 ? warp_leaf2<PV>(stk, we, Wd, sA, RS, el, sPV, lane, wkp)
+                               : warp_dfs<PV>(stk, W, Wd, we, need0, sA, RS, el, sPV, lane, wkp);
                 wtot += sub;
                 if (PV && lane == 0 && sub) atomicAdd(&sPV[e1], sub);
             }
         }
         if (lane == 0 && wtot) atomicAdd(&s_tot, wtot);
+        if (lane == 0 && wk) atomicAdd(c.work, wk);
         __syncthreads();
         const unsigned long long tot = s_tot;
         if (threadIdx.x == 0) {
@@ -531,7 +546,7 @@ kc_status launch_classes(const kc_graph* g, Ctx base, unsigned long long* cursor
             c.cursor = cursors + ci++;
             const int grid = (int)std::min<int64_t>(std::min<int64_t>(slots, q1 - q0), sms);
             k_count_cta<PV, COL, true><<<grid, NW * 32, 0, s>>>(c, W, levels, heavy, slot);
-            KC_CK(cudaGetLastError());
+            KC_LAUNCHED();
         }
     }
     // shared-memory classes, widest first
@@ -552,7 +567,7 @@ kc_status launch_classes(const kc_graph* g, Ctx base, unsigned long long* cursor
         c.cursor = cursors + ci++;
         const int grid = (int)std::min<int64_t>(q1 - q0, (int64_t)sms * blocks_per_sm(kern, NW * 32, smem));
         kern<<<grid, NW * 32, smem, s>>>(c, W, levels, nullptr, 0);
-        KC_CK(cudaGetLastError());
+        KC_LAUNCHED();
     }
     // W = 1: one warp per owner
     {
@@ -566,7 +581,7 @@ kc_status launch_classes(const kc_graph* g, Ctx base, unsigned long long* cursor
             const int64_t warps = q1 - q0;
             const int grid = (int)std::min<int64_t>((warps + 7) / 8, (int64_t)sms * blocks_per_sm(kern, 256, 0));
             kern<<<grid, 256, 0, s>>>(c);
-            KC_CK(cudaGetLastError());
+            KC_LAUNCHED();
         }
     }
     return KC_OK;
@@ -605,6 +620,7 @@ kc_status count_launch(const kc_graph* g, const CountArgs& a, unsigned long long
     c.pv = a.pv;
     c.po = a.po;
     c.cursor = nullptr;
+    c.work = a.work;
     const bool col = a.colours >= 2;  // one colour keeps every pair
     if (a.per_vertex) {
         if (col) return KC_ENOTSUP;

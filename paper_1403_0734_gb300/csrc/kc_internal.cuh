@@ -24,6 +24,15 @@ void set_cuda_error(cudaError_t e, const char* what);
         }                                                             \
     } while (0)
 
+// Every kernel launch is followed by KC_LAUNCHED(): it counts the launch
+// (process-wide, readable through kc_get_param) and checks the launch error.
+void note_launch();
+#define KC_LAUNCHED()                                                 \
+    do {                                                              \
+        ::kc::note_launch();                                          \
+        KC_CK(cudaGetLastError());                                    \
+    } while (0)
+
 #define KC_TRY(expr)                                                  \
     do {                                                              \
         kc_status kc_s_ = (expr);                                     \
@@ -93,11 +102,16 @@ struct CountArgs {
     unsigned long long* total;  // [2] 128-bit total (lo, hi)
     unsigned long long* pv;     // [n] rank space, nullable
     unsigned long long* po;     // [n] rank space, nullable
+    unsigned long long* work;   // [1] bitmap word-operations executed, nullable
 };
 
 kc_status count_launch(const kc_graph* g, const CountArgs& a, unsigned long long* cursors,
                        uint32_t* heavy_scratch, int64_t heavy_words, cudaStream_t s);
 
+extern bool g_work_enabled;
+extern unsigned long long g_last_work;
+int64_t launch_count();
+void reset_launch_count();
 int smem_max_words();
 kc_status set_smem_max_words(int64_t v);
 

@@ -378,7 +378,7 @@ kc_status orient(const int64_t* off_in, const int32_t* adj_in, int32_t n, int64_
         if (n > 0) {
             k_validate<<<grid_for((int64_t)n * 32, kThreads, sms * 16), kThreads, 0, s>>>(off, adj, n, m2,
                                                                                       (int*)(stats + 3));
-            KC_CK(cudaGetLastError());
+            KC_LAUNCHED();
         }
         unsigned long long bad = 0;
         KC_CK(cudaMemcpyAsync(&bad, stats + 3, sizeof(bad), cudaMemcpyDeviceToHost, s));
@@ -397,7 +397,7 @@ kc_status orient(const int64_t* off_in, const int32_t* adj_in, int32_t n, int64_
 
     // a1: degrees
     k_degree<<<grid_for(n, kThreads, sms * 8), kThreads, 0, s>>>(off, n, keyA, valA, (unsigned int*)stats);
-    KC_CK(cudaGetLastError());
+    KC_LAUNCHED();
     unsigned int maxdeg = 0;
     KC_CK(cudaMemcpyAsync(&maxdeg, stats, sizeof(maxdeg), cudaMemcpyDeviceToHost, s));
     KC_CK(cudaStreamSynchronize(s));
@@ -410,18 +410,18 @@ kc_status orient(const int64_t* off_in, const int32_t* adj_in, int32_t n, int64_
     KC_TRY(radix_sort_pairs(&kk, &vv, keyB, valB, n, bits, hist, hscan, stmp, s));
     KC_CK(cudaMemcpyAsync(g->perm, vv, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
     k_rank_from_perm<<<grid_for(n, kThreads, sms * 8), kThreads, 0, s>>>(g->perm, kk, n, g->rank, g->deg);
-    KC_CK(cudaGetLastError());
+    KC_LAUNCHED();
 
     // a3: |Gamma+| per rank, offsets
     k_orient_count<<<grid_for((int64_t)n * 32, kThreads, sms * 16), kThreads, 0, s>>>(off, adj, g->rank, n,
                                                                                    g->dplus);
-    KC_CK(cudaGetLastError());
+    KC_LAUNCHED();
     KC_TRY(scan_i32_to_i64(g->dplus, g->offp, n, stmp, s));
 
     // statistics + queue keys
     k_dplus_stats<<<grid_for(n, kThreads, sms * 8), kThreads, 0, s>>>(g->dplus, n, (unsigned int*)(stats + 1),
                                                                      stats + 2, keyA, valA);
-    KC_CK(cudaGetLastError());
+    KC_LAUNCHED();
     unsigned long long st[3] = {0, 0, 0};
     KC_CK(cudaMemcpyAsync(st, stats, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
     KC_CK(cudaStreamSynchronize(s));
@@ -438,7 +438,7 @@ kc_status orient(const int64_t* off_in, const int32_t* adj_in, int32_t n, int64_
     }
     KC_CK(cudaMemsetAsync(dhist, 0, ((int64_t)maxd + 1) * sizeof(int32_t), s));
     k_queue_keys<<<grid_for(n, kThreads, sms * 8), kThreads, 0, s>>>(keyA, n, maxd, dhist);
-    KC_CK(cudaGetLastError());
+    KC_LAUNCHED();
     std::vector<int32_t> h_hist((size_t)maxd + 1);
     KC_CK(cudaMemcpyAsync(h_hist.data(), dhist, ((int64_t)maxd + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     KC_CK(cudaStreamSynchronize(s));
@@ -462,22 +462,25 @@ kc_status orient(const int64_t* off_in, const int32_t* adj_in, int32_t n, int64_
     const int kBlockCap = 8192;  // 32 KB of shared memory per row
     {
         int64_t q0 = ge_at(33), q1 = ge_at(1);
-        if (q1 > q0)
+        if (q1 > q0) {
             k_fill_warp<<<grid_for((q1 - q0) * 32, kThreads, sms * 16), kThreads, 0, s>>>(
                 off, adj, g->rank, g->perm, g->queue, q0, q1, g->offp, g->adjp);
-        KC_CK(cudaGetLastError());
+            KC_LAUNCHED();
+        }
         q0 = ge_at(kBlockCap + 1);
         q1 = ge_at(33);
-        if (q1 > q0)
+        if (q1 > q0) {
             k_fill_block<<<grid_for(q1 - q0, 1, sms * 8), kThreads, kBlockCap * sizeof(int32_t), s>>>(
                 off, adj, g->rank, g->perm, g->queue, q0, q1, g->offp, g->adjp, kBlockCap);
-        KC_CK(cudaGetLastError());
+            KC_LAUNCHED();
+        }
         q0 = 0;
         q1 = ge_at(kBlockCap + 1);
-        if (q1 > q0)
+        if (q1 > q0) {
             k_fill_global<<<grid_for(q1 - q0, 1, sms * 4), kThreads, 0, s>>>(off, adj, g->rank, g->perm,
                                                                           g->queue, q0, q1, g->offp, g->adjp);
-        KC_CK(cudaGetLastError());
+            KC_LAUNCHED();
+        }
     }
     KC_CK(cudaStreamSynchronize(s));
     guard.keep = true;

@@ -103,16 +103,16 @@ kc_status scan_impl(const Tin* in, int64_t* out, int64_t n, int64_t* tmp, cudaSt
     const int64_t nb = (n + kScanTile - 1) / kScanTile;
     if (nb <= 1) {
         k_scan_tile_apply<Tin><<<1, kScanThreads, 0, s>>>(in, n, nullptr, out);
-        KC_CK(cudaGetLastError());
+        KC_LAUNCHED();
         return KC_OK;
     }
     int64_t* sums = tmp;
     int64_t* sums_scan = tmp + nb;
     k_scan_tile_sums<Tin><<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, sums);
-    KC_CK(cudaGetLastError());
+    KC_LAUNCHED();
     KC_TRY(scan_impl<int64_t>(sums, sums_scan, nb, tmp + 2 * nb + 1, s));
     k_scan_tile_apply<Tin><<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, sums_scan, out);
-    KC_CK(cudaGetLastError());
+    KC_LAUNCHED();
     return KC_OK;
 }
 
@@ -219,11 +219,11 @@ kc_status radix_sort_pairs(uint32_t** keys, int32_t** vals, uint32_t* keys_alt, 
     int32_t* v_out = vals_alt;
     for (int shift = 0; shift < bits; shift += 8) {
         k_rs_hist<<<(unsigned)ntiles, kRsThreads, 0, s>>>(k_in, n, shift, ntiles, hist);
-        KC_CK(cudaGetLastError());
+        KC_LAUNCHED();
         KC_TRY(scan_impl<int32_t>(hist, hist_scan, 256 * ntiles, tmp, s));
         k_rs_scatter<<<(unsigned)ntiles, kRsThreads, 0, s>>>(k_in, v_in, n, shift, ntiles, hist_scan,
                                                             k_out, v_out);
-        KC_CK(cudaGetLastError());
+        KC_LAUNCHED();
         uint32_t* tk = k_in; k_in = k_out; k_out = tk;
         int32_t* tv = v_in; v_in = v_out; v_out = tv;
     }

@@ -21,6 +21,8 @@ KC_DEVICE_PTRS = 0x1
 KC_VALIDATE = 0x2
 KC_MAX_K = 32
 KC_PARAM_SMEM_MAX_WORDS = 1
+KC_PARAM_LAUNCH_COUNT = 2
+KC_PARAM_WORK_COUNT = 3
 
 _P = ctypes.c_void_p
 _lib = None
@@ -201,11 +203,19 @@ def export(g: Graph, stream=None) -> dict:
             "adj_plus": out["adj_plus"][:m], "queue": out["queue"][:n]}
 
 
-def count(g: Graph, k: int, per_vertex: bool = False, per_owner: bool = False, stream=None):
+def count(g: Graph, k: int, per_vertex: bool = False, per_owner: bool = False, stream=None,
+          out_pv=None, out_po=None):
     """FFF_k on the device.  Returns (q_k, per_vertex or None, per_owner or None)
-    with host numpy uint64 arrays indexed by the caller's vertex ids."""
-    pv = np.empty(max(g.n, 1), np.uint64) if per_vertex else None
-    po = np.empty(max(g.n, 1), np.uint64) if per_owner else None
+    with host numpy uint64 arrays indexed by the caller's vertex ids.  out_pv /
+    out_po: optional preallocated host uint64 arrays of n (e.g. pinned)."""
+    if out_pv is not None:
+        pv = out_pv
+    else:
+        pv = np.empty(max(g.n, 1), np.uint64) if per_vertex else None
+    if out_po is not None:
+        po = out_po
+    else:
+        po = np.empty(max(g.n, 1), np.uint64) if per_owner else None
     tot = ctypes.c_uint64(0)
     _check(_load().kc_count(g.handle, k, 0, ctypes.byref(tot), _ptr(pv), _ptr(po), _stream_handle(stream)),
            f"kc_count(k={k})")
