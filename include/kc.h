@@ -205,6 +205,26 @@ kc_status kc_estimate_csr(const int64_t* off, const int32_t* adj, int32_t n, int
                           int k, uint32_t colours, uint64_t seed, unsigned flags,
                           uint64_t* sampled, double* estimate, void* stream);
 
+/*
+ * kc_count_static -- the total q_k of kc_count, computed without allocating
+ * any device memory.  The paper has no counterpart: this is for callers that
+ * cannot call cudaMalloc when they need a count -- a process whose memory
+ * manager has already reserved the device and accounts for every byte, or
+ * latency-critical code that must not wait on an allocation.
+ *   g, k, flags, stream  as kc_count (k = 1..KC_MAX_K); no per-vertex or
+ *              per-owner outputs
+ *   total      out: q_k; host pointer, or with KC_DEVICE_PTRS a device array
+ *              of two uint64 words (low, high)
+ * Scratch comes from one 16 MiB __device__ array in the library, held by every
+ * GPU that loads it until exit.  The first call on each device looks up the
+ * array's device address (make it before any stream capture).  All calls
+ * share the array: calls that overlap on the GPU race and must be
+ * serialised by the caller.  A graph whose widest owner needs a global tile
+ * larger than the array returns KC_ENOTSUP without running.
+ * Errors: as kc_count, plus KC_ENOTSUP.
+ */
+kc_status kc_count_static(const kc_graph* g, int k, unsigned flags, uint64_t* total, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

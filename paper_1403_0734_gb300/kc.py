@@ -77,6 +77,8 @@ def _load():
     lib.kc_estimate_csr.argtypes = [_P, _P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int, ctypes.c_uint32,
                                     ctypes.c_uint64, ctypes.c_uint, _P, _P, _P]
     lib.kc_estimate_csr.restype = st
+    lib.kc_count_static.argtypes = [_P, ctypes.c_int, ctypes.c_uint, _P, _P]
+    lib.kc_count_static.restype = st
     lib.kc_set_param.argtypes = [ctypes.c_int, ctypes.c_int64]
     lib.kc_set_param.restype = st
     lib.kc_get_param.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int64)]
@@ -270,3 +272,13 @@ def estimate_csr(off, adj, k: int, colours: int, seed: int, validate: bool = Fal
                                    ctypes.byref(s), ctypes.byref(est), _stream_handle(stream)),
            f"kc_estimate_csr(k={k})")
     return int(s.value), float(est.value)
+
+
+def count_static(g: Graph, k: int, stream=None) -> int:
+    """q_k like count(), but without any device allocation (kc_count_static):
+    for callers that cannot allocate device memory when they count.  Calls
+    share one static scratch array and must not overlap on the GPU."""
+    tot = ctypes.c_uint64(0)
+    _check(_load().kc_count_static(g.handle, k, 0, ctypes.byref(tot), _stream_handle(stream)),
+           f"kc_count_static(k={k})")
+    return int(tot.value)
