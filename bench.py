@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["kc", "reference"], default="kc")
     ap.add_argument("--ks", default="3,4,5,6")
+    ap.add_argument("--algo", choices=["dfs", "pivot"], default="dfs",
+                    help="Reduce 3 counter (ordered DFS or pivoting clique tree)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0,
@@ -216,6 +218,7 @@ def main():
         dist.barrier()
     import paper_1403_0734_gb300 as kc
 
+    kc.set_param(kc.KC_PARAM_ALGO, kc.KC_ALGO_DFS if args.algo == "dfs" else kc.KC_ALGO_PIVOT)
     g = kcgen.chung_lu_1m(seed=1 + rank)
     off_d = torch.from_numpy(g.off).cuda()
     adj_d = torch.from_numpy(g.adj).cuda()
@@ -354,7 +357,7 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "n": g.n, "m": g.m, "ks": ks,
                            "l2": "flushed between timed steps (512 MiB write)",
-                           "parallelism": f"replicas x{world} (one graph per rank)"},
+                           "parallelism": f"replicas x{world} (one graph per rank)", "counter": args.algo},
                 "edges_per_s": m_all / (ms_all * 1e-3), "orient_ms": om, "per_k": per_k,
                 "roofline": roofline, "orient_roofline": orient_roof, "clocks": clocks,
                 "gpu_launches": launches, "e2e": e2e, "cpu_baseline": cpu}

@@ -185,11 +185,20 @@ kc_status kc_estimate(const kc_graph* g, int k, uint32_t colours, uint64_t seed,
  *       counting kernels; read: bitmap word-operations (a 32-bit AND plus
  *       population count) executed by the last synchronous kc_count /
  *       kc_estimate on this process while counting was on.
+ *   KC_PARAM_ALGO  the Reduce 3 counter used by kc_count / kc_estimate:
+ *       KC_ALGO_DFS (default) enumerates ordered chains x_i1 < x_i2 < ... and
+ *       closes the last two levels by population counts; KC_ALGO_PIVOT walks
+ *       G+(u) with Bron-Kerbosch pivoting and counts each leaf by binomial
+ *       coefficients (fewer nodes on near-complete G+(u)).  Both give
+ *       identical results.
  * kc_set_param returns KC_EINVAL for an unknown knob or a value out of range.
  */
 #define KC_PARAM_SMEM_MAX_WORDS 1
 #define KC_PARAM_LAUNCH_COUNT   2
 #define KC_PARAM_WORK_COUNT     3
+#define KC_PARAM_ALGO           4
+#define KC_ALGO_PIVOT 0
+#define KC_ALGO_DFS   1
 kc_status kc_set_param(int param, int64_t value);
 kc_status kc_get_param(int param, int64_t* value);
 

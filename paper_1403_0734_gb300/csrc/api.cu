@@ -152,8 +152,8 @@ kc_status run_count(const kc_graph* g, int k, uint32_t colours, uint64_t seed, u
             KC_TRY(sc.get(&po_rank, n));
             KC_CK(cudaMemsetAsync(po_rank, 0, (size_t)n * sizeof(unsigned long long), s));
         }
-        int slots = 0;
-        const int64_t hw = heavy_scratch_words(g, k, &slots);
+        int64_t slot_words = 0;
+        const int64_t hw = heavy_scratch_words(g, k, &slot_words);
         uint32_t* heavy = nullptr;
         if (hw > 0) KC_TRY(sc.get(&heavy, hw));
         CountArgs a;
@@ -333,6 +333,7 @@ kc_status kc_set_param(int param, int64_t value)
         kc::reset_launch_count();
         return KC_OK;
     }
+    if (param == KC_PARAM_ALGO) return kc::set_count_algo(value);
     if (param == KC_PARAM_WORK_COUNT) {
         if (value != 0 && value != 1) return KC_EINVAL;
         kc::g_work_enabled = value != 0;
@@ -350,6 +351,10 @@ kc_status kc_get_param(int param, int64_t* value)
     }
     if (param == KC_PARAM_LAUNCH_COUNT) {
         *value = kc::launch_count();
+        return KC_OK;
+    }
+    if (param == KC_PARAM_ALGO) {
+        *value = kc::count_algo();
         return KC_OK;
     }
     if (param == KC_PARAM_WORK_COUNT) {

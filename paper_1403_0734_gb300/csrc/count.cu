@@ -25,7 +25,7 @@
 #include <algorithm>
 #include <climits>
 
-#include "kc_internal.cuh"
+#include "count_common.cuh"
 
 namespace kc {
 
@@ -36,6 +36,21 @@ static int g_smem_max_words = kNumSmemClasses > 0 ? kClassWords[kNumSmemClasses 
 
 int smem_max_words() { return g_smem_max_words; }
 
+// Process-wide choice of the Reduce 3 counter: the ordered depth-first search
+// (default) or the pivoting clique tree.
+static int g_algo = KC_ALGO_DFS;
+int count_algo() { return g_algo; }
+kc_status set_count_algo(int64_t v)
+{
+    if (v != KC_ALGO_PIVOT && v != KC_ALGO_DFS) return KC_EINVAL;
+    g_algo = (int)v;
+    return KC_OK;
+}
+
+int64_t sct_heavy_words(const kc_graph* g, int k, int64_t nheavy);
+kc_status sct_launch(const kc_graph* g, const CountArgs& a, const cc::Ctx& c, unsigned long long* cursors,
+                     uint32_t* heavy, int64_t heavy_words, cudaStream_t s);
+
 kc_status set_smem_max_words(int64_t v)
 {
     if (v < 1 || v > kClassWords[kNumSmemClasses - 1]) return KC_EINVAL;
@@ -45,51 +60,12 @@ kc_status set_smem_max_words(int64_t v)
 
 namespace {
 
-struct Ctx {
-    const int64_t* __restrict__ offp;
-    const int32_t* __restrict__ adjp;
-    const int32_t* __restrict__ queue;
-    const int32_t* __restrict__ perm;
-    int64_t q0, q1;
-    int k;
-    uint32_t colours;
-    uint64_t seed;
-    unsigned long long* total;
-    unsigned long long* pv;
-    unsigned long long* po;
-    unsigned long long* cursor;
-    unsigned long long* work;  // nullable: bitmap word-operations executed
-};
-
-// colour(u, x): splitmix64 output function over seed ^ (G * (u<<32 | x)),
-// reduced to [0, c) by a 64x64 multiply-high (Sec. 6; spec in kc.h).
-__device__ __forceinline__ uint32_t colour_of(uint64_t seed, int32_t u, int32_t x, uint32_t c)
-{
-    uint64_t key = ((uint64_t)(uint32_t)u << 32) | (uint64_t)(uint32_t)x;
-    uint64_t z = seed ^ (0x9E3779B97F4A7C15ull * key);
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    z ^= z >> 31;
-    return (uint32_t)__umul64hi(z, (uint64_t)c);
-}
-
-// 128-bit total as (lo, hi) words.
-__device__ __forceinline__ void add_total(unsigned long long* t, unsigned long long v)
-{
-    if (v == 0) return;
-    unsigned long long old = atomicAdd(&t[0], v);
-    if (old + v < old) atomicAdd(&t[1], 1ull);
-}
-
-__device__ __forceinline__ unsigned long long warp_sum64(unsigned long long v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-    return v;
-}
-
-__device__ __forceinline__ uint32_t mask_above(int b) { return b >= 31 ? 0u : (kFull << (b + 1)); }
-__device__ __forceinline__ uint32_t mask_below(int b) { return (1u << b) - 1u; }
+using cc::Ctx;
+using cc::add_total;
+using cc::colour_of;
+using cc::mask_above;
+using cc::mask_below;
+using cc::warp_sum64;
 
 // ------------------------------------------------------------ W = 1 class
 
@@ -120,41 +96,12 @@ __global__ void __launch_bounds__(256) k_count_w1(Ctx c)
         const int64_t b = c.offp[r];
         const int d = (int)(c.offp[r + 1] - b);
         const int32_t x = lane < d ? c.adjp[b + lane] : INT_MAX;
-        const int32_t maxL = __shfl_sync(kFull, x, d - 1);
         uint32_t col = 0;
         if (COL && lane < d) col = colour_of(c.seed, c.perm[r], c.perm[x], c.colours);
 
         // (b) rows: lane j searches x_j in each 32-entry chunk of Gamma+(x_i)
-        uint32_t up = 0;
-        for (int i = 0; i < d - 1; ++i) {
-            const int32_t xi = __shfl_sync(kFull, x, i);
-            const int64_t s0 = c.offp[xi], s1 = c.offp[xi + 1];
-            uint32_t row = 0;
-            for (int64_t p0 = s0; p0 < s1; p0 += 32) {
-                const int64_t p = p0 + lane;
-                const int32_t y = p < s1 ? c.adjp[p] : INT_MAX;
-                int lo = 0;
-#pragma unroll
-                for (int step = 16; step > 0; step >>= 1) {
-                    const int32_t yy = __shfl_sync(kFull, y, lo + step - 1);
-                    if (yy < x) lo += step;
-                }
-                const int32_t yl = __shfl_sync(kFull, y, lo);
-                row |= __ballot_sync(kFull, lane > i && lane < d && yl == x);
-                if (__shfl_sync(kFull, y, 31) >= maxL) break;
-            }
-            if (COL) row &= __ballot_sync(kFull, col == __shfl_sync(kFull, col, i));
-            if (lane == i) up = row;
-        }
-        uint32_t A = up;
-        if (PV) {
-            uint32_t low = 0;
-            for (int j = 1; j < d; ++j) {
-                const uint32_t colj = __ballot_sync(kFull, (up >> j) & 1u);
-                if (lane == j) low = colj;
-            }
-            A = up | low;
-        }
+        const uint32_t up = cc::build_rows_w1<COL>(c, x, d, col, lane);
+        const uint32_t A = PV ? (up | cc::lower_rows_w1(up, d, lane)) : up;
 
         // (c) depth-first search; level t's state of the chain is kept in lane t
         unsigned long long tot = 0, pvl = 0, wk = 0;
@@ -405,31 +352,10 @@ __global__ void __launch_bounds__(256) k_count_cta(Ctx c, int W, int levels, uin
             s_tot = 0ull;
         }
         __syncthreads();
-        const int32_t maxL = sL[d - 1];
         const int Wd = (d + 31) >> 5;  // words in use by this owner
 
         // (b) + (d): rows, split over warps
-        for (int i = wid; i < d - 1; i += NW) {
-            const int32_t xi = sL[i];
-            const int64_t s0 = c.offp[xi], s1 = c.offp[xi + 1];
-            const uint32_t ci = COL ? sCol[i] : 0u;
-            for (int64_t p0 = s0; p0 < s1; p0 += 32) {
-                const int64_t pp = p0 + lane;
-                const int32_t y = pp < s1 ? c.adjp[pp] : INT_MAX;
-                if (y <= maxL) {
-                    int lo = i + 1, hi = d;
-                    while (lo < hi) {
-                        const int mid = (lo + hi) >> 1;
-                        if (sL[mid] < y) lo = mid + 1; else hi = mid;
-                    }
-                    if (lo < d && sL[lo] == y && (!COL || sCol[lo] == ci)) {
-                        atomicOr(&sA[(int64_t)i * RS + (lo >> 5)], 1u << (lo & 31));
-                        if (PV) atomicOr(&sA[(int64_t)lo * RS + (i >> 5)], 1u << (i & 31));
-                    }
-                }
-                if (__shfl_sync(kFull, y, 31) >= maxL) break;
-            }
-        }
+        cc::build_rows<PV, COL>(c, sL, sCol, d, sA, RS, wid, NW, lane);
         __syncthreads();
 
         // (c) count
@@ -499,15 +425,6 @@ __global__ void __launch_bounds__(256) k_count_cta(Ctx c, int W, int levels, uin
     }
 }
 
-template <typename K>
-int blocks_per_sm(K kernel, int threads, size_t smem)
-{
-    int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, smem) != cudaSuccess || nb < 1)
-        nb = 1;
-    return nb;
-}
-
 int warps_for_width(int W)
 {
     if (W <= 2) return 2;
@@ -565,7 +482,7 @@ kc_status launch_classes(const kc_graph* g, Ctx base, unsigned long long* cursor
         c.q0 = q0;
         c.q1 = q1;
         c.cursor = cursors + ci++;
-        const int grid = (int)std::min<int64_t>(q1 - q0, (int64_t)sms * blocks_per_sm(kern, NW * 32, smem));
+        const int grid = (int)std::min<int64_t>(q1 - q0, (int64_t)sms * cc::blocks_per_sm(kern, NW * 32, smem));
         kern<<<grid, NW * 32, smem, s>>>(c, W, levels, nullptr, 0);
         KC_LAUNCHED();
     }
@@ -579,7 +496,7 @@ kc_status launch_classes(const kc_graph* g, Ctx base, unsigned long long* cursor
             c.cursor = cursors + ci++;
             auto kern = k_count_w1<PV, COL>;
             const int64_t warps = q1 - q0;
-            const int grid = (int)std::min<int64_t>((warps + 7) / 8, (int64_t)sms * blocks_per_sm(kern, 256, 0));
+            const int grid = (int)std::min<int64_t>((warps + 7) / 8, (int64_t)sms * cc::blocks_per_sm(kern, 256, 0));
             kern<<<grid, 256, 0, s>>>(c);
             KC_LAUNCHED();
         }
@@ -589,18 +506,23 @@ kc_status launch_classes(const kc_graph* g, Ctx base, unsigned long long* cursor
 
 }  // namespace
 
-int64_t heavy_scratch_words(const kc_graph* g, int k, int* slots_out)
+int64_t heavy_scratch_words(const kc_graph* g, int k, int64_t* slot_words)
 {
-    *slots_out = 0;
+    *slot_words = 0;
     const int64_t cut = 32LL * smem_max_words();
     if (g->max_dplus <= cut || k - 1 > g->max_dplus) return 0;
     const int64_t nheavy = g->ge[(size_t)std::max<int64_t>(cut + 1, k - 1)];
     if (nheavy <= 0) return 0;
+    if (count_algo() == KC_ALGO_PIVOT) {
+        const int64_t total = sct_heavy_words(g, k, nheavy);
+        *slot_words = sct_heavy_words(g, k, 1);
+        return total;
+    }
     const int W = (g->max_dplus + 31) / 32;
     const int levels = k > 3 ? k - 3 : 1;
     const Layout lay = make_layout(W, W, 8, levels, true, true);
     const int64_t slots = std::min<int64_t>(nheavy, num_sms());
-    *slots_out = (int)slots;
+    *slot_words = lay.total;
     return lay.total * slots;
 }
 
@@ -622,6 +544,7 @@ kc_status count_launch(const kc_graph* g, const CountArgs& a, unsigned long long
     c.cursor = nullptr;
     c.work = a.work;
     const bool col = a.colours >= 2;  // one colour keeps every pair
+    if (count_algo() == KC_ALGO_PIVOT) return sct_launch(g, a, c, cursors, heavy_scratch, heavy_words, s);
     if (a.per_vertex) {
         if (col) return KC_ENOTSUP;
         return launch_classes<true, false>(g, c, cursors, heavy_scratch, heavy_words, s);

@@ -1,0 +1,147 @@
+// count_common.cuh -- device helpers shared by the counting kernels (the
+// ordered DFS in count.cu and the pivoting counter in sct.cu): launch
+// context, the colour hash of cFFF_k, 128-bit total accumulation, and the
+// G+(u) bitmap builders.
+#pragma once
+
+#include <climits>
+
+#include "kc_internal.cuh"
+
+namespace kc {
+namespace cc {
+
+struct Ctx {
+    const int64_t* __restrict__ offp;
+    const int32_t* __restrict__ adjp;
+    const int32_t* __restrict__ queue;
+    const int32_t* __restrict__ perm;
+    int64_t q0, q1;
+    int k;
+    uint32_t colours;
+    uint64_t seed;
+    unsigned long long* total;
+    unsigned long long* pv;
+    unsigned long long* po;
+    unsigned long long* cursor;
+    unsigned long long* work;  // nullable: bitmap word-operations executed
+};
+
+// colour(u, x): splitmix64 output function over seed ^ (G * (u<<32 | x)),
+// reduced to [0, c) by a 64x64 multiply-high (Sec. 6; spec in kc.h).
+__device__ __forceinline__ uint32_t colour_of(uint64_t seed, int32_t u, int32_t x, uint32_t c)
+{
+    uint64_t key = ((uint64_t)(uint32_t)u << 32) | (uint64_t)(uint32_t)x;
+    uint64_t z = seed ^ (0x9E3779B97F4A7C15ull * key);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return (uint32_t)__umul64hi(z, (uint64_t)c);
+}
+
+// 128-bit total as (lo, hi) words.
+__device__ __forceinline__ void add_total(unsigned long long* t, unsigned long long v)
+{
+    if (v == 0) return;
+    unsigned long long old = atomicAdd(&t[0], v);
+    if (old + v < old) atomicAdd(&t[1], 1ull);
+}
+
+__device__ __forceinline__ unsigned long long warp_sum64(unsigned long long v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+__device__ __forceinline__ uint32_t mask_above(int b) { return b >= 31 ? 0u : (kFull << (b + 1)); }
+__device__ __forceinline__ uint32_t mask_below(int b) { return (1u << b) - 1u; }
+
+
+// Rows of G+(u) for an owner with d <= 32 (Map 2 pairs kept by Reduce 2):
+// lane j holds x_j (rank, INT_MAX past d); returns, in lane i, the word whose
+// bit j (j > i) is set iff x_j is in Gamma+(x_i) -- each Gamma+(x_i) chunk of
+// 32 entries is searched for x_j by a shuffle binary search, and the scan
+// stops at max Gamma+(u).  cFFF_k keeps only pairs of equal colour.
+template <bool COL>
+__device__ __forceinline__ uint32_t build_rows_w1(const Ctx& c, int32_t x, int d, uint32_t col, int lane)
+{
+    const int32_t maxL = __shfl_sync(kFull, x, d - 1);
+    uint32_t up = 0;
+    for (int i = 0; i < d - 1; ++i) {
+        const int32_t xi = __shfl_sync(kFull, x, i);
+        const int64_t s0 = c.offp[xi], s1 = c.offp[xi + 1];
+        uint32_t row = 0;
+        for (int64_t p0 = s0; p0 < s1; p0 += 32) {
+            const int64_t p = p0 + lane;
+            const int32_t y = p < s1 ? c.adjp[p] : INT_MAX;
+            int lo = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                const int32_t yy = __shfl_sync(kFull, y, lo + step - 1);
+                if (yy < x) lo += step;
+            }
+            const int32_t yl = __shfl_sync(kFull, y, lo);
+            row |= __ballot_sync(kFull, lane > i && lane < d && yl == x);
+            if (__shfl_sync(kFull, y, 31) >= maxL) break;
+        }
+        if (COL) row &= __ballot_sync(kFull, col == __shfl_sync(kFull, col, i));
+        if (lane == i) up = row;
+    }
+    return up;
+}
+
+// Lower half of the symmetric G+(u) bitmap from the upper rows (bit i of
+// row j for every i < j with bit j in row i).
+__device__ __forceinline__ uint32_t lower_rows_w1(uint32_t up, int d, int lane)
+{
+    uint32_t low = 0;
+    for (int j = 1; j < d; ++j) {
+        const uint32_t colj = __ballot_sync(kFull, (up >> j) & 1u);
+        if (lane == j) low = colj;
+    }
+    return low;
+}
+
+// Rows of G+(u) into a bitmap A (row stride RS words, zeroed beforehand) by
+// warps w0, w0+nw, ... of the caller; sL holds Gamma+(u) (ranks, ascending),
+// sCol their colours under cFFF_k.  With SYM the bitmap is made symmetric.
+template <bool SYM, bool COL>
+__device__ __forceinline__ void build_rows(const Ctx& c, const int32_t* sL, const uint32_t* sCol, int d,
+                                           uint32_t* A, int RS, int w0, int nw, int lane)
+{
+    const int32_t maxL = sL[d - 1];
+    for (int i = w0; i < d - 1; i += nw) {
+        const int32_t xi = sL[i];
+        const int64_t s0 = c.offp[xi], s1 = c.offp[xi + 1];
+        const uint32_t ci = COL ? sCol[i] : 0u;
+        for (int64_t p0 = s0; p0 < s1; p0 += 32) {
+            const int64_t pp = p0 + lane;
+            const int32_t y = pp < s1 ? c.adjp[pp] : INT_MAX;
+            if (y <= maxL) {
+                int lo = i + 1, hi = d;
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (sL[mid] < y) lo = mid + 1; else hi = mid;
+                }
+                if (lo < d && sL[lo] == y && (!COL || sCol[lo] == ci)) {
+                    atomicOr(&A[(int64_t)i * RS + (lo >> 5)], 1u << (lo & 31));
+                    if (SYM) atomicOr(&A[(int64_t)lo * RS + (i >> 5)], 1u << (i & 31));
+                }
+            }
+            if (__shfl_sync(kFull, y, 31) >= maxL) break;
+        }
+    }
+}
+
+template <typename K>
+inline int blocks_per_sm(K kernel, int threads, size_t smem)
+{
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, smem) != cudaSuccess || nb < 1)
+        nb = 1;
+    return nb;
+}
+
+}  // namespace cc
+}  // namespace kc

@@ -115,7 +115,11 @@ void reset_launch_count();
 int smem_max_words();
 kc_status set_smem_max_words(int64_t v);
 
-// Words of global scratch the heavy (global-bitmap) class needs.
-int64_t heavy_scratch_words(const kc_graph* g, int k, int* slots_out);
+int count_algo();
+kc_status set_count_algo(int64_t v);
+
+// Words of global scratch the heavy (global-bitmap) class needs for k under
+// the current settings; *slot_words receives the size of one tile slot.
+int64_t heavy_scratch_words(const kc_graph* g, int k, int64_t* slot_words);
 
 }  // namespace kc

@@ -96,11 +96,10 @@ extern "C" kc_status kc_count_static(const kc_graph* g, int k, unsigned flags, u
     uint32_t* tiles = (uint32_t*)((char*)base + kSmallBytes);
     const int64_t tile_words = (int64_t)((kStaticScratchBytes - kSmallBytes) / sizeof(uint32_t));
 
-    int slots = 0;
-    const int64_t need = kc::heavy_scratch_words(g, k, &slots);
+    int64_t per_slot = 0;
+    const int64_t need = kc::heavy_scratch_words(g, k, &per_slot);
     int64_t use_words = 0;
     if (need > 0) {
-        const int64_t per_slot = need / slots;
         if (per_slot > tile_words) return KC_ENOTSUP;  // widest owner does not fit the static array
         use_words = need < tile_words ? need : (tile_words / per_slot) * per_slot;
     }

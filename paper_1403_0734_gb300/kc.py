@@ -23,6 +23,9 @@ KC_MAX_K = 32
 KC_PARAM_SMEM_MAX_WORDS = 1
 KC_PARAM_LAUNCH_COUNT = 2
 KC_PARAM_WORK_COUNT = 3
+KC_PARAM_ALGO = 4
+KC_ALGO_PIVOT = 0
+KC_ALGO_DFS = 1
 
 _P = ctypes.c_void_p
 _lib = None

@@ -82,3 +82,9 @@ def test_params(lib):
             kc.set_param(kc.KC_PARAM_SMEM_MAX_WORDS, bad)
     with pytest.raises(kc.KcError):
         kc.set_param(99, 1)
+    assert kc.get_param(kc.KC_PARAM_ALGO) == kc.KC_ALGO_DFS
+    kc.set_param(kc.KC_PARAM_ALGO, kc.KC_ALGO_PIVOT)
+    assert kc.get_param(kc.KC_PARAM_ALGO) == kc.KC_ALGO_PIVOT
+    kc.set_param(kc.KC_PARAM_ALGO, kc.KC_ALGO_DFS)
+    with pytest.raises(kc.KcError):
+        kc.set_param(kc.KC_PARAM_ALGO, 7)

@@ -18,8 +18,9 @@ import oracle
 pytestmark = pytest.mark.gpu
 
 
-@pytest.fixture(scope="module")
-def kc():
+@pytest.fixture(scope="module", params=["pivot", "dfs"])
+def kc(request):
+    """The library, once with each Reduce 3 counter (pivoting tree, ordered DFS)."""
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
@@ -27,8 +28,10 @@ def kc():
     kb.build()
     import paper_1403_0734_gb300 as kc
     kc.set_param(kc.KC_PARAM_SMEM_MAX_WORDS, 32)
+    kc.set_param(kc.KC_PARAM_ALGO, kc.KC_ALGO_PIVOT if request.param == "pivot" else kc.KC_ALGO_DFS)
     yield kc
     kc.set_param(kc.KC_PARAM_SMEM_MAX_WORDS, 32)
+    kc.set_param(kc.KC_PARAM_ALGO, kc.KC_ALGO_DFS)
 
 
 def elem_sym(values, k):
