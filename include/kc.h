@@ -191,12 +191,17 @@ kc_status kc_estimate(const kc_graph* g, int k, uint32_t colours, uint64_t seed,
  *       G+(u) with Bron-Kerbosch pivoting and counts each leaf by binomial
  *       coefficients (fewer nodes on near-complete G+(u)).  Both give
  *       identical results.
+ *   KC_PARAM_COMPACT_LO, KC_PARAM_COMPACT_HI  candidate sets of the ordered
+ *       search with LO..HI elements (HI <= 64, default 1..64; HI = 0 off) are
+ *       finished on a compact register copy of their induced subgraph.
  * kc_set_param returns KC_EINVAL for an unknown knob or a value out of range.
  */
 #define KC_PARAM_SMEM_MAX_WORDS 1
 #define KC_PARAM_LAUNCH_COUNT   2
 #define KC_PARAM_WORK_COUNT     3
 #define KC_PARAM_ALGO           4
+#define KC_PARAM_COMPACT_LO     5
+#define KC_PARAM_COMPACT_HI     6
 #define KC_ALGO_PIVOT 0
 #define KC_ALGO_DFS   1
 kc_status kc_set_param(int param, int64_t value);

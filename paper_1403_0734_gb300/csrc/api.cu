@@ -334,6 +334,8 @@ kc_status kc_set_param(int param, int64_t value)
         return KC_OK;
     }
     if (param == KC_PARAM_ALGO) return kc::set_count_algo(value);
+    if (param == KC_PARAM_COMPACT_LO) return kc::set_compact_window(value, kc::compact_hi());
+    if (param == KC_PARAM_COMPACT_HI) return kc::set_compact_window(kc::compact_lo(), value);
     if (param == KC_PARAM_WORK_COUNT) {
         if (value != 0 && value != 1) return KC_EINVAL;
         kc::g_work_enabled = value != 0;
@@ -355,6 +357,14 @@ kc_status kc_get_param(int param, int64_t* value)
     }
     if (param == KC_PARAM_ALGO) {
         *value = kc::count_algo();
+        return KC_OK;
+    }
+    if (param == KC_PARAM_COMPACT_LO) {
+        *value = kc::compact_lo();
+        return KC_OK;
+    }
+    if (param == KC_PARAM_COMPACT_HI) {
+        *value = kc::compact_hi();
         return KC_OK;
     }
     if (param == KC_PARAM_WORK_COUNT) {

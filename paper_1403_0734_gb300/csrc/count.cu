@@ -48,6 +48,8 @@ kc_status set_count_algo(int64_t v)
 }
 
 int64_t sct_heavy_words(const kc_graph* g, int k, int64_t nheavy);
+bool dfs_reg_supported(int k);
+kc_status dfs_reg_launch(const cc::Ctx& c, int W, bool pv, bool col, cudaStream_t s);
 kc_status sct_launch(const kc_graph* g, const CountArgs& a, const cc::Ctx& c, unsigned long long* cursors,
                      uint32_t* heavy, int64_t heavy_words, cudaStream_t s);
 
@@ -473,15 +475,19 @@ kc_status launch_classes(const kc_graph* g, Ctx base, unsigned long long* cursor
         const int64_t dlo = 32LL * kClassWords[cl - 1] + 1, dhi = 32LL * W;
         const int64_t q0 = ge_at(dhi + 1), q1 = ge_at(std::max(dlo, dmin));
         if (q1 <= q0) continue;
+        Ctx c = base;
+        c.q0 = q0;
+        c.q1 = q1;
+        c.cursor = cursors + ci++;
+        if (dfs_reg_supported(k)) {  // register-resident search
+            KC_TRY(dfs_reg_launch(c, W, PV, COL, s));
+            continue;
+        }
         const int NW = warps_for_width(W);
         const Layout lay = make_layout(W, W + 1, NW, levels, PV, COL);
         const size_t smem = (size_t)lay.total * 4;
         auto kern = k_count_cta<PV, COL, false>;
         if (smem > 48 * 1024) KC_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        Ctx c = base;
-        c.q0 = q0;
-        c.q1 = q1;
-        c.cursor = cursors + ci++;
         const int grid = (int)std::min<int64_t>(q1 - q0, (int64_t)sms * cc::blocks_per_sm(kern, NW * 32, smem));
         kern<<<grid, NW * 32, smem, s>>>(c, W, levels, nullptr, 0);
         KC_LAUNCHED();

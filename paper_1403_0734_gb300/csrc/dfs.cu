@@ -1,0 +1,502 @@
+// dfs.cu -- ordered depth-first counter (Reduce 3, Alg. 1; Sec. 3) for owners
+// whose G+(u) bitmap fits in shared memory (|Gamma+(u)| <= 1024), k <= 8.
+//
+// Same search as the generic kernel in count.cu -- chains x_i1 < x_i2 < ...
+// of G+(u) with candidate sets C_t = C_{t-1} & row(i_t), the last two levels
+// closed by population counts -- laid out for instruction efficiency:
+//   * a candidate set lives in registers, lane w holding its word w, so an
+//     intersection is one shared load and one AND per lane, and the stack of
+//     the search (at most k-3 levels) is a register array;
+//   * the last level picks its elements by rank (a warp prefix scan of word
+//     population counts, a shuffle binary search and __fns), so no list of
+//     elements is written to shared memory;
+//   * the per-element word loop is uniform across the warp: every lane reads
+//     the same candidate word by a broadcast shuffle and its own row word;
+//   * memberships accumulate in 32-bit shared counters with a carry word;
+//   * once a candidate set has at most 64 elements and at least three more
+//     vertices are to be chosen, its induced subgraph is compressed into
+//     64-bit rows (one ballot per row; lane j holds the rows of elements j
+//     and j+32) and the rest of that sub-tree runs on registers only.
+// Work items are (owner u, part c) with c < R: the item's CTA builds G+(u)
+// in shared memory (its warps together), then its warps take the first-level
+// vertices i1 = c, c+R, c+2R, ... from a shared counter.  R > 1 splits a heavy
+// owner's count across CTAs by first-level vertex -- the postponed,
+// neighbour-keyed counting of heavy G+(u) proposed in Sec. 7 -- so that the
+// largest owners do not leave the rest of the GPU idle at the end.
+#include <algorithm>
+
+#include "count_common.cuh"
+
+namespace kc {
+
+int num_sms();
+
+namespace {
+
+using cc::add_total;
+using cc::colour_of;
+using cc::Ctx;
+using cc::mask_above;
+using cc::mask_below;
+
+constexpr int kMaxLev = 5;  // register stack levels: k - 3 <= 5, i.e. k <= 8
+
+}  // namespace
+
+// Size window [lo, hi] (hi <= 64) of candidate sets that switch to the compact
+// sub-tree; hi = 0 turns the compact mode off.
+static int g_compact_lo = 1, g_compact_hi = 64;
+int compact_lo() { return g_compact_lo; }
+int compact_hi() { return g_compact_hi; }
+kc_status set_compact_window(int64_t lo, int64_t hi)
+{
+    if (lo < 1 || hi < 0 || hi > 64) return KC_EINVAL;
+    g_compact_lo = (int)lo;
+    g_compact_hi = (int)hi;
+    return KC_OK;
+}
+
+namespace {
+
+struct RLayout {
+    int64_t L, col, pvlo, pvhi, A, total;
+};
+
+__host__ __device__ inline RLayout make_rlayout(int W, int RS, bool pv, bool col)
+{
+    const int64_t D = 32LL * W;
+    RLayout l;
+    l.L = 0;
+    l.col = l.L + D;
+    l.pvlo = l.col + (col ? D : 0);
+    l.pvhi = l.pvlo + (pv ? D : 0);
+    l.A = l.pvhi + (pv ? D : 0);
+    l.total = l.A + D * RS;
+    return l;
+}
+
+// 64-bit membership increment as 32-bit shared atomics with a carry word.
+__device__ __forceinline__ void pv_add(uint32_t* lo, uint32_t* hi, int e, unsigned long long v)
+{
+    const uint32_t v0 = (uint32_t)v, v1 = (uint32_t)(v >> 32);
+    if (v0) {
+        const uint32_t old = atomicAdd(&lo[e], v0);
+        if (old + v0 < old) atomicAdd(&hi[e], 1u);
+    }
+    if (v1) atomicAdd(&hi[e], v1);
+}
+
+__device__ __forceinline__ uint32_t st_get(const uint32_t (&st)[kMaxLev], int t)
+{
+    uint32_t v = st[0];
+#pragma unroll
+    for (int i = 1; i < kMaxLev; ++i)
+        if (t == i) v = st[i];
+    return v;
+}
+
+__device__ __forceinline__ void st_set(uint32_t (&st)[kMaxLev], int t, uint32_t v)
+{
+#pragma unroll
+    for (int i = 0; i < kMaxLev; ++i)
+        if (t == i) st[i] = v;
+}
+
+// Edges inside C (lane w holds word w; words below w0 and from Wd on are 0).
+// Every element e of C takes one lane and sums popc(C & row(e)) over the
+// words: with upper-triangular rows that is the number of higher neighbours
+// of e in C, and the sum over e is the edge count; with symmetric rows
+// (per-vertex mode) it is e's degree inside C -- its membership increment --
+// and the edge count is half the sum.
+template <bool PV>
+__device__ __forceinline__ uint32_t leaf2_reg(uint32_t C, int w0, int Wd, const uint32_t* A, int RS,
+                                              uint32_t* pvlo, uint32_t* pvhi, int lane,
+                                              unsigned long long* wk)
+{
+    const uint32_t pc = (uint32_t)__popc(C);
+    uint32_t pre = pc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(kFull, pre, o);
+        if (lane >= o) pre += t;
+    }
+    const uint32_t total = __shfl_sync(kFull, pre, 31);
+    const uint32_t excl = pre - pc;
+    uint32_t S = 0;
+    for (uint32_t base = 0; base < total; base += 32) {
+        const uint32_t j = base + (uint32_t)lane;
+        // word of the j-th element: first lane whose inclusive count exceeds j
+        int w = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            const uint32_t pv_ = __shfl_sync(kFull, pre, w + step - 1);
+            if (pv_ <= j) w += step;
+        }
+        const uint32_t cw = __shfl_sync(kFull, C, w);
+        const uint32_t ex = __shfl_sync(kFull, excl, w);
+        const bool valid = j < total;
+        const int e = w * 32 + (valid ? (int)__fns(cw, 0, (int)(j - ex) + 1) : 0);
+        const uint32_t* Ae = A + (int64_t)(valid ? e : 0) * RS;
+        // upper rows hold nothing below the first element's word of the pass
+        const int xs = PV ? w0 : __shfl_sync(kFull, w, 0);
+        uint32_t f = 0;
+#pragma unroll 4
+        for (int x = xs; x < Wd; ++x) f += (uint32_t)__popc(__shfl_sync(kFull, C, x) & (valid ? Ae[x] : 0u));
+        if (valid) {
+            S += f;
+            if (PV && f) pv_add(pvlo, pvhi, e, f);
+        }
+        if (wk) *wk += (unsigned long long)__reduce_add_sync(kFull, valid ? (unsigned)(Wd - xs) : 0u);
+    }
+    const uint32_t E = __reduce_add_sync(kFull, S);
+    return PV ? E / 2u : E;
+}
+
+// ------------------------------------------------ compact sub-tree (<= 64)
+
+__device__ __forceinline__ unsigned long long mask64_above(int b) { return b >= 63 ? 0ull : (~0ull << (b + 1)); }
+
+// Row of compact vertex v (held by lane v & 31, word v >> 5).
+__device__ __forceinline__ unsigned long long crow(unsigned long long r0, unsigned long long r1, int v)
+{
+    const unsigned long long a = __shfl_sync(kFull, r0, v & 31);
+    const unsigned long long b = __shfl_sync(kFull, r1, v & 31);
+    return v < 32 ? a : b;
+}
+
+// Edges inside the compact set C.  Per-vertex mode: each member's degree
+// inside C (full rows f) is its membership increment and the edge count is
+// half their sum; otherwise the upper rows u count higher neighbours.
+template <bool PV>
+__device__ __forceinline__ unsigned long long cleaf2(unsigned long long C, unsigned long long u0,
+                                                     unsigned long long u1, unsigned long long f0,
+                                                     unsigned long long f1, int lane, unsigned long long& a0,
+                                                     unsigned long long& a1)
+{
+    const bool in0 = (C >> lane) & 1ull, in1 = (C >> (lane + 32)) & 1ull;
+    if (PV) {
+        const unsigned d0 = in0 ? (unsigned)__popcll(C & f0) : 0u;
+        const unsigned d1 = in1 ? (unsigned)__popcll(C & f1) : 0u;
+        a0 += d0;
+        a1 += d1;
+        return (unsigned long long)(__reduce_add_sync(kFull, d0 + d1) / 2u);
+    }
+    unsigned e = 0;
+    if (in0) e += (unsigned)__popcll(C & u0);
+    if (in1) e += (unsigned)__popcll(C & u1);
+    return (unsigned long long)__reduce_add_sync(kFull, e);
+}
+
+// Cliques of `need` (>= 2) vertices chosen from the n-vertex compact graph
+// (upper rows u, full rows f in per-vertex mode), with memberships in a0/a1.
+template <bool PV>
+__device__ unsigned long long cdfs(unsigned long long u0, unsigned long long u1, unsigned long long f0,
+                                   unsigned long long f1, int n, int need, int lane, unsigned long long& a0,
+                                   unsigned long long& a1, unsigned long long* wk)
+{
+    const unsigned long long all = n >= 64 ? ~0ull : ((1ull << n) - 1ull);
+    if (need == 2) {
+        if (wk) *wk += (unsigned long long)n * (PV ? 4 : 2);
+        return cleaf2<PV>(all, u0, u1, f0, f1, lane, a0, a1);
+    }
+    unsigned long long tot = 0, cur = all, cur_sub = 0;
+    unsigned long long st_rem = 0, st_sub = 0;
+    int st_e = 0, t = 0;
+    for (;;) {
+        if (cur == 0ull) {
+            if (t == 0) break;
+            const unsigned long long sdone = cur_sub;
+            --t;
+            cur = __shfl_sync(kFull, st_rem, t);
+            const int pe = __shfl_sync(kFull, st_e, t);
+            cur_sub = __shfl_sync(kFull, st_sub, t) + sdone;
+            if (PV && lane == (pe & 31)) {
+                if (pe < 32) a0 += sdone; else a1 += sdone;
+            }
+            continue;
+        }
+        const int e = __ffsll((long long)cur) - 1;
+        cur &= cur - 1ull;
+        const unsigned long long Cn = cur & crow(u0, u1, e);
+        const int nd = need - t - 1;
+        if (wk) *wk += 2;
+        if (__popcll(Cn) < nd) continue;
+        if (nd == 2) {
+            if (wk) *wk += (unsigned long long)__popcll(Cn) * (PV ? 4 : 2);
+            const unsigned long long E = cleaf2<PV>(Cn, u0, u1, f0, f1, lane, a0, a1);
+            tot += E;
+            cur_sub += E;
+            if (PV && lane == (e & 31)) {
+                if (e < 32) a0 += E; else a1 += E;
+            }
+        } else {
+            if (lane == t) {
+                st_rem = cur;
+                st_e = e;
+                st_sub = cur_sub;
+            }
+            ++t;
+            cur = Cn;
+            cur_sub = 0;
+        }
+    }
+    return tot;
+}
+
+// The sub-tree below a candidate set C (lane w holds word w, n = |C| <= 64
+// elements, `need` >= 3 vertices still to choose), on a compact copy of G[C].
+template <bool PV>
+__device__ unsigned long long compact_count(uint32_t C, int n, int need, const uint32_t* A, int RS,
+                                            uint32_t* pvlo, uint32_t* pvhi, int lane, unsigned long long* wk)
+{
+    // elements p_j (lane j: p_j and p_{j+32}) by rank
+    const uint32_t pc = (uint32_t)__popc(C);
+    uint32_t pre = pc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(kFull, pre, o);
+        if (lane >= o) pre += t;
+    }
+    const uint32_t excl = pre - pc;
+    int p[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const uint32_t j = (uint32_t)(lane + 32 * h);
+        int w = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            const uint32_t pv_ = __shfl_sync(kFull, pre, w + step - 1);
+            if (pv_ <= j) w += step;
+        }
+        const uint32_t cw = __shfl_sync(kFull, C, w);
+        const uint32_t ex = __shfl_sync(kFull, excl, w);
+        p[h] = j < (uint32_t)n ? w * 32 + (int)__fns(cw, 0, (int)(j - ex) + 1) : 0;
+    }
+    // compact rows: bit j of row i = adjacency of p_i and p_j
+    unsigned long long r0 = 0, r1 = 0;
+    for (int i = 0; i < n; ++i) {
+        const int pi = __shfl_sync(kFull, i < 32 ? p[0] : p[1], i & 31);
+        const uint32_t* Ai = A + (int64_t)pi * RS;
+        const bool b0 = lane < n && ((Ai[p[0] >> 5] >> (p[0] & 31)) & 1u);
+        const bool b1 = lane + 32 < n && ((Ai[p[1] >> 5] >> (p[1] & 31)) & 1u);
+        const unsigned long long row =
+            (unsigned long long)__ballot_sync(kFull, b0) | ((unsigned long long)__ballot_sync(kFull, b1) << 32);
+        if (lane == (i & 31)) {
+            if (i < 32) r0 = row; else r1 = row;
+        }
+    }
+    if (wk) *wk += (unsigned long long)n * 2;
+    const unsigned long long u0 = r0 & mask64_above(lane), u1 = r1 & mask64_above(lane + 32);
+    unsigned long long a0 = 0, a1 = 0;
+    const unsigned long long tot = cdfs<PV>(u0, u1, r0, r1, n, need, lane, a0, a1, wk);
+    if (PV) {
+        if (a0 && lane < n) pv_add(pvlo, pvhi, p[0], a0);
+        if (a1 && lane + 32 < n) pv_add(pvlo, pvhi, p[1], a1);
+    }
+    return tot;
+}
+
+// Chains below a first-level choice: level 0 holds C (elements above i1),
+// need0 >= 3 vertices still to choose.  Returns the cliques completed and
+// credits chain members with their sub-tree totals (per-vertex mode).
+template <bool PV>
+__device__ unsigned long long dfs_reg(uint32_t c0, int need0, int Wd, const uint32_t* A, int RS, uint32_t* pvlo,
+                                      uint32_t* pvhi, int lane, unsigned long long* wk, int clo, int chi)
+{
+    uint32_t st[kMaxLev];
+#pragma unroll
+    for (int i = 0; i < kMaxLev; ++i) st[i] = 0u;
+    st[0] = c0;
+    int t = 0;
+    unsigned long long total = 0, cur_sub = 0, f_sub = 0;
+    int f_e = 0;  // lane t: chain element chosen at level t
+    for (;;) {
+        uint32_t rem = st_get(st, t);
+        const uint32_t nz = __ballot_sync(kFull, rem != 0u);
+        if (nz == 0u) {
+            if (t == 0) break;
+            const unsigned long long sdone = cur_sub;
+            --t;
+            const int pe = __shfl_sync(kFull, f_e, t);
+            cur_sub = __shfl_sync(kFull, f_sub, t) + sdone;
+            if (PV && lane == 0 && sdone) pv_add(pvlo, pvhi, pe, sdone);
+            continue;
+        }
+        const int fw = __ffs(nz) - 1;
+        const uint32_t vw = __shfl_sync(kFull, rem, fw);
+        const int e = fw * 32 + __ffs(vw) - 1;
+        if (lane == fw) rem &= rem - 1u;
+        st_set(st, t, rem);
+        const uint32_t* Ae = A + (int64_t)e * RS;
+        const uint32_t cn = (lane >= fw && lane < Wd) ? (rem & Ae[lane]) : 0u;
+        const int cnt = (int)__reduce_add_sync(kFull, (unsigned)__popc(cn));
+        if (wk) *wk += (unsigned long long)(Wd - fw);
+        const int need = need0 - t - 1;
+        if (cnt < need) continue;
+        if (need == 2 || (cnt >= clo && cnt <= chi)) {
+            const unsigned long long E = need == 2 ? leaf2_reg<PV>(cn, fw, Wd, A, RS, pvlo, pvhi, lane, wk)
+                                                   : compact_count<PV>(cn, cnt, need, A, RS, pvlo, pvhi, lane, wk);
+            total += E;
+            cur_sub += E;
+            if (PV && lane == 0 && E) pv_add(pvlo, pvhi, e, E);
+        } else {
+            if (lane == t) {
+                f_e = e;
+                f_sub = cur_sub;
+            }
+            ++t;
+            st_set(st, t, cn);
+            cur_sub = 0;
+        }
+    }
+    return total;
+}
+
+template <bool PV, bool COL>
+__global__ void __launch_bounds__(256, 4) k_dfs_reg(Ctx c, int W, int R, int clo, int chi)
+{
+    extern __shared__ __align__(16) uint32_t smem[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, NW = blockDim.x >> 5;
+    const int RS = W + 1;
+    const RLayout lay = make_rlayout(W, RS, PV, COL);
+    int32_t* sL = (int32_t*)(smem + lay.L);
+    uint32_t* sCol = smem + lay.col;
+    uint32_t* pvlo = smem + lay.pvlo;
+    uint32_t* pvhi = smem + lay.pvhi;
+    uint32_t* sA = smem + lay.A;
+    __shared__ int s_next;
+    __shared__ unsigned long long s_tot, s_wk;
+    __shared__ long long s_item;
+    const int r0 = c.k - 1;
+    unsigned long long* wkp_dummy = nullptr;
+    (void)wkp_dummy;
+
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (long long)atomicAdd(c.cursor, 1ull);
+        __syncthreads();
+        const int64_t q = c.q0 + s_item / R;
+        const int part = (int)(s_item % R);
+        if (q >= c.q1) break;
+        const int32_t r = c.queue[q];
+        const int64_t b = c.offp[r];
+        const int d = (int)(c.offp[r + 1] - b);
+        const int Wd = (d + 31) >> 5;
+        const int32_t ur = COL ? c.perm[r] : 0;
+        for (int j = threadIdx.x; j < d; j += blockDim.x) {
+            const int32_t x = c.adjp[b + j];
+            sL[j] = x;
+            if (COL) sCol[j] = colour_of(c.seed, ur, c.perm[x], c.colours);
+            if (PV) {
+                pvlo[j] = 0u;
+                pvhi[j] = 0u;
+            }
+        }
+        for (int64_t j = threadIdx.x; j < (int64_t)d * RS; j += blockDim.x) sA[j] = 0u;
+        if (threadIdx.x == 0) {
+            s_next = 0;
+            s_tot = 0ull;
+            s_wk = 0ull;
+        }
+        __syncthreads();
+        cc::build_rows<PV, COL>(c, sL, sCol, d, sA, RS, wid, NW, lane);
+        __syncthreads();
+
+        unsigned long long wtot = 0, wk = 0;
+        unsigned long long* wkp = c.work ? &wk : nullptr;
+        if (r0 == 2) {  // k = 3: edges of G+(u)
+            for (int e = part + wid * R; e < d; e += NW * R) {
+                const uint32_t* Ae = sA + (int64_t)e * RS;
+                const int we = e >> 5, be = e & 31;
+                uint32_t up = 0, all = 0;
+                if (lane < Wd) {
+                    const uint32_t v = Ae[lane];
+                    up = lane > we ? (uint32_t)__popc(v) : (lane == we ? (uint32_t)__popc(v & mask_above(be)) : 0u);
+                    all = (uint32_t)__popc(v);
+                }
+                up = __reduce_add_sync(kFull, up);
+                wtot += up;
+                if (PV) {
+                    all = __reduce_add_sync(kFull, all);
+                    if (lane == 0 && all) pv_add(pvlo, pvhi, e, all);
+                }
+                if (wkp) wk += (unsigned long long)(PV ? Wd : Wd - we);
+            }
+        } else {
+            const int need0 = r0 - 1;
+            for (;;) {
+                int e1 = 0;
+                if (lane == 0) e1 = part + R * atomicAdd(&s_next, 1);
+                e1 = __shfl_sync(kFull, e1, 0);
+                if (e1 >= d) break;
+                const int we = e1 >> 5, be = e1 & 31;
+                uint32_t c0 = 0u;
+                if (lane >= we && lane < Wd) {
+                    c0 = sA[(int64_t)e1 * RS + lane];
+                    if (lane == we) c0 &= mask_above(be);
+                }
+                const int cnt = (int)__reduce_add_sync(kFull, (unsigned)__popc(c0));
+                if (wkp) wk += (unsigned long long)(Wd - we);
+                if (cnt < need0) continue;
+                const unsigned long long sub =
+                    need0 == 2 ? (unsigned long long)leaf2_reg<PV>(c0, we, Wd, sA, RS, pvlo, pvhi, lane, wkp)
+                    : (cnt >= clo && cnt <= chi) ? compact_count<PV>(c0, cnt, need0, sA, RS, pvlo, pvhi, lane, wkp)
+                                                 : dfs_reg<PV>(c0, need0, Wd, sA, RS, pvlo, pvhi, lane, wkp, clo, chi);
+                wtot += sub;
+                if (PV && lane == 0 && sub) pv_add(pvlo, pvhi, e1, sub);
+            }
+        }
+        if (lane == 0 && wtot) atomicAdd(&s_tot, wtot);
+        if (lane == 0 && wk) atomicAdd(&s_wk, wk);
+        __syncthreads();
+        const unsigned long long tot = s_tot;
+        if (threadIdx.x == 0) {
+            add_total(c.total, tot);
+            if (c.po && tot) atomicAdd(&c.po[r], tot);  // R parts add up
+            if (PV && tot) atomicAdd(&c.pv[r], tot);
+            if (c.work && s_wk) atomicAdd(c.work, s_wk);
+        }
+        if (PV)
+            for (int j = threadIdx.x; j < d; j += blockDim.x) {
+                const unsigned long long v = ((unsigned long long)pvhi[j] << 32) | pvlo[j];
+                if (v) atomicAdd(&c.pv[sL[j]], v);
+            }
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+bool dfs_reg_supported(int k) { return k >= 3 && k - 3 <= kMaxLev; }
+
+// Parts per owner: heavy owners (rows of 8+ words) are split for k >= 5,
+// where one owner's search can outlast the rest of the class.
+int parts_per_owner(int W, int k)
+{
+    if (k < 5) return 1;
+    if (W >= 16) return 16;
+    if (W >= 8) return 4;
+    return 1;
+}
+
+// Launch the shared-memory class of width W (words) over queue range [q0, q1).
+kc_status dfs_reg_launch(const cc::Ctx& c, int W, bool pv, bool col, cudaStream_t s)
+{
+    const int sms = num_sms();
+    const int R = parts_per_owner(W, c.k);
+    const int NW = W <= 4 ? 4 : 8;
+    const RLayout lay = make_rlayout(W, W + 1, pv, col);
+    const size_t smem = (size_t)lay.total * 4;
+    auto pick = [&](auto kern) -> kc_status {
+        if (smem > 48 * 1024)
+            KC_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        const int grid =
+            (int)std::min<int64_t>((c.q1 - c.q0) * R, (int64_t)sms * cc::blocks_per_sm(kern, NW * 32, smem));
+        kern<<<grid, NW * 32, smem, s>>>(c, W, R, g_compact_lo, g_compact_hi);
+        KC_LAUNCHED();
+        return KC_OK;
+    };
+    if (pv) return col ? KC_ENOTSUP : pick(k_dfs_reg<true, false>);
+    return col ? pick(k_dfs_reg<false, true>) : pick(k_dfs_reg<false, false>);
+}
+
+}  // namespace kc

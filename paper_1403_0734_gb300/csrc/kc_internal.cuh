@@ -115,6 +115,9 @@ void reset_launch_count();
 int smem_max_words();
 kc_status set_smem_max_words(int64_t v);
 
+int compact_lo();
+int compact_hi();
+kc_status set_compact_window(int64_t lo, int64_t hi);
 int count_algo();
 kc_status set_count_algo(int64_t v);
 

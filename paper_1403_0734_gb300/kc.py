@@ -24,6 +24,8 @@ KC_PARAM_SMEM_MAX_WORDS = 1
 KC_PARAM_LAUNCH_COUNT = 2
 KC_PARAM_WORK_COUNT = 3
 KC_PARAM_ALGO = 4
+KC_PARAM_COMPACT_LO = 5
+KC_PARAM_COMPACT_HI = 6
 KC_ALGO_PIVOT = 0
 KC_ALGO_DFS = 1
 
