@@ -275,14 +275,8 @@ def main():
         assert int(pv[k].sum().item()) == k * q[k] and int(po[k].sum().item()) == q[k]
     cliques = sum(q.values())
     ms = statistics.mean(step_ms)
-    t = torch.tensor([ms, float(cliques), float(g.m)], dtype=torch.float64, device="cuda")
-    if world > 1:
-        tmax = t.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        ms_all, cliques_all, m_all = float(tmax[0]), float(t[1]), float(t[2])
-    else:
-        ms_all, cliques_all, m_all = ms, float(cliques), float(g.m)
+    from paper_1403_0734_gb300 import dist as kd
+    ms_all, (cliques_all, m_all) = kd.reduce_step_stats(ms, [cliques, g.m])
 
     # roofline of the dominant call (counting at the largest k), untimed work count
     kmax = max(ks)

@@ -175,6 +175,47 @@ kc_status kc_estimate(const kc_graph* g, int k, uint32_t colours, uint64_t seed,
                       uint64_t* per_owner, void* stream);
 
 /*
+ * kc_footprint -- device memory a kc_count / kc_estimate call on g for k
+ * allocates (stream-ordered) while it runs, for admission control.
+ *   per_vertex, per_owner  nonzero if those outputs are requested
+ *   host_outputs           nonzero if outputs are host arrays
+ *   bytes                  out
+ * Errors: KC_EINVAL.
+ */
+kc_status kc_footprint(const kc_graph* g, int k, int per_vertex, int per_owner, int host_outputs,
+                       uint64_t* bytes);
+
+/*
+ * kc_count_part -- the share of kc_count contributed by one part of the
+ * owners: owners are split by their position in the work queue (|Gamma+|
+ * descending), position i belonging to part i mod nparts, so the parts are
+ * balanced.  Every clique is counted by exactly one owner (Sec. 3), so the
+ * totals, per-vertex and per-owner arrays of parts 0..nparts-1 add up to
+ * kc_count's.  This is how the count is sharded over GPUs (each GPU holds a
+ * replica of the oriented graph and counts one part; the partial totals are
+ * summed).
+ *   k          3..KC_MAX_K
+ *   part       0..nparts-1; other arguments as kc_count
+ * Errors: as kc_count.
+ */
+kc_status kc_count_part(const kc_graph* g, int k, int part, int nparts, unsigned flags, uint64_t* total,
+                        uint64_t* per_vertex, uint64_t* per_owner, void* stream);
+
+/*
+ * kc_count_batch -- kc_count's total for each of ng graphs (all on one
+ * device) in a single launch sequence: the owners of all graphs form one
+ * queue per owner class, so many small, uneven graphs fill the GPU together
+ * instead of one launch each.
+ *   gs      host array of ng graph handles
+ *   totals  out: host array of ng counts, or with KC_DEVICE_PTRS a device
+ *           array of 2*ng words (low, high per graph)
+ * Synchronous.  Errors: KC_EINVAL (a NULL handle, graphs on different
+ * devices), KC_ENOMEM, KC_EOVERFLOW (some count), KC_ECUDA.
+ */
+kc_status kc_count_batch(const kc_graph* const* gs, int ng, int k, unsigned flags, uint64_t* totals,
+                         void* stream);
+
+/*
  * Tuning knobs (process-wide; they change speed, never results).
  *   KC_PARAM_SMEM_MAX_WORDS  owners whose bitmap rows need at most this many
  *       32-bit words (|Gamma+(u)| <= 32 * value) keep G+(u) in shared memory;

@@ -215,3 +215,37 @@ def chung_lu_1m(seed: int = 1) -> Graph:
 def sbm_2m(seed: int = 1, p_in: float = 0.3) -> Graph:
     """SBM, n=2*10^6, 40000 blocks of 50, p_in=0.3, m_total=5*10^7."""
     return sbm(2_000_000, 50, p_in, 50_000_000, seed)
+
+
+# --- batched workload: many uneven Chung-Lu graphs --------------------------
+
+def _sm64(x: int) -> int:
+    """splitmix64 output for state x (integer arithmetic, platform independent)."""
+    z = (x + 0x9E3779B97F4A7C15) & 0xFFFFFFFFFFFFFFFF
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & 0xFFFFFFFFFFFFFFFF
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & 0xFFFFFFFFFFFFFFFF
+    return z ^ (z >> 31)
+
+
+def batch_params(num: int, seed: int = 1, nmin: int = 50, nmax: int = 20000, dmin: float = 8.0,
+                 dmax: float = 64.0):
+    """Per-graph (n, m, wmax, seed) of the batched workload: n log-uniform in
+    [nmin, nmax], average degree uniform in [dmin, dmax], m = n * degree / 2,
+    maximum Chung-Lu weight sqrt(2m); graph g is drawn with seed g + 1."""
+    import math
+    out = []
+    for g in range(num):
+        a = _sm64((seed << 32) ^ (2 * g)) >> 11
+        b = _sm64((seed << 32) ^ (2 * g + 1)) >> 11
+        u, v = a / 2.0 ** 53, b / 2.0 ** 53
+        n = int(round(math.exp(math.log(nmin) + u * (math.log(nmax) - math.log(nmin)))))
+        deg = dmin + v * (dmax - dmin)
+        m = max(1, int(n * deg / 2))
+        m = min(m, n * (n - 1) // 2)
+        out.append((n, m, max(1.0, math.sqrt(2.0 * m)), g + 1))
+    return out
+
+
+def batch_workload(num: int, seed: int = 1, gamma: float = 2.3, **kw):
+    """The uneven batch: Chung-Lu graphs (exponent gamma) with batch_params."""
+    return [chung_lu(n, m, gamma, wmax, s) for (n, m, wmax, s) in batch_params(num, seed, **kw)]

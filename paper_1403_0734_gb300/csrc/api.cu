@@ -6,7 +6,7 @@
 #include <new>
 #include <vector>
 
-#include "kc_internal.cuh"
+#include "count_common.cuh"
 
 namespace kc {
 
@@ -104,7 +104,8 @@ kc_status copy_out_u64(uint64_t* dst, const unsigned long long* src, int32_t n, 
 
 // Shared body of kc_count and kc_estimate.
 kc_status run_count(const kc_graph* g, int k, uint32_t colours, uint64_t seed, unsigned flags,
-                    uint64_t* total, uint64_t* per_vertex, uint64_t* per_owner, cudaStream_t s)
+                    uint64_t* total, uint64_t* per_vertex, uint64_t* per_owner, cudaStream_t s, int part = 0,
+                    int nparts = 1)
 {
     const bool dev = (flags & KC_DEVICE_PTRS) != 0;
     const int32_t n = g->n;
@@ -125,6 +126,7 @@ kc_status run_count(const kc_graph* g, int k, uint32_t colours, uint64_t seed, u
         else KC_TRY(sc.get(&out_po, n));
     }
 
+    if (k <= 2 && nparts > 1) return KC_ENOTSUP;  // q_1, q_2 have no owner split
     if (k <= 2) {
         const unsigned long long q = k == 1 ? (unsigned long long)n : (unsigned long long)g->m;
         k_fill_u64<<<1, 32, 0, s>>>(small, 1, q);
@@ -165,6 +167,8 @@ kc_status run_count(const kc_graph* g, int k, uint32_t colours, uint64_t seed, u
         a.pv = pv_rank;
         a.po = po_rank;
         a.work = g_work_enabled ? small + 10 : nullptr;
+        a.part = part;
+        a.nparts = nparts;
         KC_TRY(count_launch(g, a, small + 2, heavy, hw, s));
         if (pv_rank) {
             k_permute_u64<<<grid1d(n), 256, 0, s>>>(pv_rank, g->perm, n, out_pv);
@@ -323,6 +327,104 @@ kc_status kc_estimate(const kc_graph* g, int k, uint32_t colours, uint64_t seed,
         *estimate = (double)*sampled * f;
     }
     return KC_OK;
+}
+
+kc_status kc_footprint(const kc_graph* g, int k, int per_vertex, int per_owner, int host_outputs,
+                       uint64_t* bytes)
+{
+    if (!g || !bytes || k < 1 || k > KC_MAX_K) return KC_EINVAL;
+    const uint64_t n = (uint64_t)(g->n > 0 ? g->n : 1);
+    uint64_t b = 256;  // total, cursors, work counter
+    const uint64_t arrays = (per_vertex ? 1 : 0) + (per_owner ? 1 : 0);
+    if (k >= 3) b += arrays * n * 8;           // rank-space accumulators
+    if (host_outputs) b += arrays * n * 8;     // staging for the copy back
+    if (k >= 3) {
+        int64_t slot_words = 0;
+        b += (uint64_t)kc::heavy_scratch_words(g, k, &slot_words) * 4;
+    }
+    *bytes = b;
+    return KC_OK;
+}
+
+kc_status kc_count_part(const kc_graph* g, int k, int part, int nparts, unsigned flags, uint64_t* total,
+                        uint64_t* per_vertex, uint64_t* per_owner, void* stream)
+{
+    if (!g || !total || k < 3 || k > KC_MAX_K || nparts < 1 || part < 0 || part >= nparts) return KC_EINVAL;
+    kc::DeviceGuard dg(g->device);
+    return kc::run_count(g, k, 0, 0, flags, total, per_vertex, per_owner, (cudaStream_t)stream, part, nparts);
+}
+
+kc_status kc_count_batch(const kc_graph* const* gs, int ng, int k, unsigned flags, uint64_t* totals, void* stream)
+{
+    if (!gs || ng < 0 || !totals || k < 1 || k > KC_MAX_K) return KC_EINVAL;
+    if (ng == 0) return KC_OK;
+    for (int i = 0; i < ng; ++i)
+        if (!gs[i] || gs[i]->device != gs[0]->device) return KC_EINVAL;
+    kc::DeviceGuard dg(gs[0]->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool dev = (flags & KC_DEVICE_PTRS) != 0;
+    if (k <= 2) {
+        std::vector<unsigned long long> h((size_t)(dev ? 2 * ng : ng), 0ull);
+        for (int i = 0; i < ng; ++i) {
+            const unsigned long long q = k == 1 ? (unsigned long long)gs[i]->n : (unsigned long long)gs[i]->m;
+            h[(size_t)(dev ? 2 * i : i)] = q;
+        }
+        if (dev) {
+            KC_CK(cudaMemcpyAsync(totals, h.data(), h.size() * sizeof(uint64_t), cudaMemcpyHostToDevice, s));
+            KC_CK(cudaStreamSynchronize(s));
+        } else {
+            std::copy(h.begin(), h.end(), totals);
+        }
+        return KC_OK;
+    }
+    kc::Scratch sc(s);
+    std::vector<kc::cc::GraphDesc> hd((size_t)ng);
+    int Wh = 1;
+    int64_t nheavy = 0;
+    for (int i = 0; i < ng; ++i) {
+        hd[(size_t)i] = {gs[i]->offp, gs[i]->adjp, gs[i]->queue, gs[i]->perm};
+        Wh = std::max(Wh, (gs[i]->max_dplus + 31) / 32);
+        int64_t q0 = 0, q1 = 0;
+        kc::class_range(gs[i], k, 0, &q0, &q1);
+        nheavy += q1 - q0;
+    }
+    kc::cc::GraphDesc* dd = nullptr;
+    int64_t* tables = nullptr;
+    unsigned long long* small = nullptr;  // cursors [0..15], then 2 words per graph
+    KC_TRY(sc.get(&dd, ng));
+    KC_TRY(sc.get(&tables, (int64_t)kc::kOwnerSlots * (2 * ng + 1)));
+    KC_TRY(sc.get(&small, 16 + 2 * (int64_t)ng));
+    KC_CK(cudaMemcpyAsync(dd, hd.data(), hd.size() * sizeof(kc::cc::GraphDesc), cudaMemcpyHostToDevice, s));
+    KC_CK(cudaMemsetAsync(small, 0, (16 + 2 * (size_t)ng) * sizeof(unsigned long long), s));
+    int64_t slot_words = 0;
+    const int64_t hw = kc::heavy_scratch_words_w(Wh, k, nheavy, &slot_words);
+    uint32_t* heavy = nullptr;
+    if (hw > 0) KC_TRY(sc.get(&heavy, hw));
+    kc::CountArgs a;
+    a.k = k;
+    a.colours = 0;
+    a.seed = 0;
+    a.per_vertex = false;
+    a.total = small + 16;
+    a.pv = nullptr;
+    a.po = nullptr;
+    a.work = nullptr;
+    std::vector<int64_t> host_tables;
+    KC_TRY(kc::count_batch_launch(gs, ng, a, dd, tables, small, heavy, hw, host_tables, s));
+    std::vector<unsigned long long> th((size_t)(2 * ng));
+    if (dev) {
+        KC_CK(cudaMemcpyAsync(totals, small + 16, 2 * (size_t)ng * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+        KC_CK(cudaStreamSynchronize(s));  // host tables are read by the copy above
+        return KC_OK;
+    }
+    KC_CK(cudaMemcpyAsync(th.data(), small + 16, th.size() * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+    KC_CK(cudaStreamSynchronize(s));
+    kc_status st = KC_OK;
+    for (int i = 0; i < ng; ++i) {
+        totals[i] = th[(size_t)(2 * i)];
+        if (th[(size_t)(2 * i + 1)]) st = KC_EOVERFLOW;
+    }
+    return st;
 }
 
 kc_status kc_set_param(int param, int64_t value)

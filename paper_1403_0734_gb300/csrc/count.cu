@@ -47,11 +47,11 @@ kc_status set_count_algo(int64_t v)
     return KC_OK;
 }
 
-int64_t sct_heavy_words(const kc_graph* g, int k, int64_t nheavy);
+int64_t sct_heavy_words_w(int W, int k, int64_t nheavy);
+kc_status sct_launch_slot(int slot, int Wh, const cc::Ctx& c, bool pv, bool col, uint32_t* heavy,
+                          int64_t heavy_words, cudaStream_t s);
 bool dfs_reg_supported(int k);
 kc_status dfs_reg_launch(const cc::Ctx& c, int W, bool pv, bool col, cudaStream_t s);
-kc_status sct_launch(const kc_graph* g, const CountArgs& a, const cc::Ctx& c, unsigned long long* cursors,
-                     uint32_t* heavy, int64_t heavy_words, cudaStream_t s);
 
 kc_status set_smem_max_words(int64_t v)
 {
@@ -84,17 +84,17 @@ __device__ __forceinline__ unsigned long long leaf2_w1(uint32_t C, uint32_t up, 
 }
 
 template <bool PV, bool COL>
-__global__ void __launch_bounds__(256) k_count_w1(Ctx c)
+__global__ void __launch_bounds__(256) k_count_w1(Ctx cb)
 {
     const int lane = threadIdx.x & 31;
-    const int r0 = c.k - 1;  // vertices to choose inside G+(u)
+    const int r0 = cb.k - 1;  // vertices to choose inside G+(u)
     for (;;) {
         unsigned long long pos = 0;
-        if (lane == 0) pos = atomicAdd(c.cursor, 1ull);
+        if (lane == 0) pos = atomicAdd(cb.cursor, 1ull);
         pos = __shfl_sync(kFull, pos, 0);
-        const int64_t q = c.q0 + (int64_t)pos;
-        if (q >= c.q1) break;
-        const int32_t r = c.queue[q];
+        Ctx c;
+        int32_t r;
+        if (!cc::resolve(cb, (int64_t)pos, c, r)) break;
         const int64_t b = c.offp[r];
         const int d = (int)(c.offp[r + 1] - b);
         const int32_t x = lane < d ? c.adjp[b + lane] : INT_MAX;
@@ -314,7 +314,7 @@ __host__ __device__ inline Layout make_layout(int W, int RS, int NW, int levels,
 }
 
 template <bool PV, bool COL, bool HEAVY>
-__global__ void __launch_bounds__(256) k_count_cta(Ctx c, int W, int levels, uint32_t* gscratch,
+__global__ void __launch_bounds__(256) k_count_cta(Ctx cb, int W, int levels, uint32_t* gscratch,
                                                    int64_t slot_words)
 {
     extern __shared__ __align__(16) uint32_t smem[];
@@ -332,13 +332,13 @@ __global__ void __launch_bounds__(256) k_count_cta(Ctx c, int W, int levels, uin
     __shared__ unsigned long long s_tot;
     __shared__ long long s_item;
 
-    const int r0 = c.k - 1;
+    const int r0 = cb.k - 1;
     for (;;) {
-        if (threadIdx.x == 0) s_item = (long long)atomicAdd(c.cursor, 1ull);
+        if (threadIdx.x == 0) s_item = (long long)atomicAdd(cb.cursor, 1ull);
         __syncthreads();
-        const int64_t q = c.q0 + s_item;
-        if (q >= c.q1) break;
-        const int32_t r = c.queue[q];
+        Ctx c;
+        int32_t r;
+        if (!cc::resolve(cb, (int64_t)s_item, c, r)) break;
         const int64_t b = c.offp[r];
         const int d = (int)(c.offp[r + 1] - b);
         const int32_t ur = COL ? c.perm[r] : 0;
@@ -434,113 +434,73 @@ int warps_for_width(int W)
     return 8;
 }
 
+// One owner class of the ordered DFS: slot 0 = global tiles (rows wider than
+// the shared-memory limit), slots 1..5 = shared-memory rows of 32, 16, 8, 4, 2
+// words, slot 6 = one word (registers).  Wh is the global-tile row width.
 template <bool PV, bool COL>
-kc_status launch_classes(const kc_graph* g, Ctx base, unsigned long long* cursors, uint32_t* heavy,
-                         int64_t heavy_words, cudaStream_t s)
+kc_status launch_slot_dfs(int slot, int Wh, const Ctx& c, uint32_t* heavy, int64_t heavy_words, cudaStream_t s)
 {
+    if (c.nitems <= 0) return KC_OK;
     const int sms = num_sms();
-    const int k = base.k;
+    const int k = c.k;
     const int levels = k > 3 ? k - 3 : 1;
-    auto ge_at = [&](int64_t t) -> int64_t {
-        if (t <= 0) return g->n;
-        return t <= (int64_t)g->max_dplus ? g->ge[(size_t)t] : 0;
-    };
-    const int64_t dmin = k - 1;  // Reduce 1 filter
-    const int maxw = smem_max_words();
-    int ci = 0;
-
-    // heavy: rows wider than the shared-memory limit, global tiles
-    {
-        const int64_t q1 = ge_at(std::max<int64_t>(32LL * maxw + 1, dmin)), q0 = 0;
-        if (q1 > q0) {
-            const int W = (g->max_dplus + 31) / 32;
-            const int NW = 8;
-            const Layout lay = make_layout(W, W, NW, levels, PV, COL);
-            const int64_t slot = lay.total;
-            const int64_t slots = heavy_words / slot;
-            if (slots < 1) return KC_ENOMEM;
-            Ctx c = base;
-            c.q0 = q0;
-            c.q1 = q1;
-            c.cursor = cursors + ci++;
-            const int grid = (int)std::min<int64_t>(std::min<int64_t>(slots, q1 - q0), sms);
-            k_count_cta<PV, COL, true><<<grid, NW * 32, 0, s>>>(c, W, levels, heavy, slot);
-            KC_LAUNCHED();
-        }
-    }
-    // shared-memory classes, widest first
-    for (int cl = kNumSmemClasses - 1; cl >= 1; --cl) {
-        const int W = kClassWords[cl];
-        if (W > maxw) continue;
-        const int64_t dlo = 32LL * kClassWords[cl - 1] + 1, dhi = 32LL * W;
-        const int64_t q0 = ge_at(dhi + 1), q1 = ge_at(std::max(dlo, dmin));
-        if (q1 <= q0) continue;
-        Ctx c = base;
-        c.q0 = q0;
-        c.q1 = q1;
-        c.cursor = cursors + ci++;
-        if (dfs_reg_supported(k)) {  // register-resident search
-            KC_TRY(dfs_reg_launch(c, W, PV, COL, s));
-            continue;
-        }
-        const int NW = warps_for_width(W);
-        const Layout lay = make_layout(W, W + 1, NW, levels, PV, COL);
-        const size_t smem = (size_t)lay.total * 4;
-        auto kern = k_count_cta<PV, COL, false>;
-        if (smem > 48 * 1024) KC_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        const int grid = (int)std::min<int64_t>(q1 - q0, (int64_t)sms * cc::blocks_per_sm(kern, NW * 32, smem));
-        kern<<<grid, NW * 32, smem, s>>>(c, W, levels, nullptr, 0);
+    if (slot == 0) {
+        const int NW = 8;
+        const Layout lay = make_layout(Wh, Wh, NW, levels, PV, COL);
+        const int64_t nslots = heavy_words / lay.total;
+        if (nslots < 1) return KC_ENOMEM;
+        const int grid = (int)std::min<int64_t>(std::min<int64_t>(nslots, c.nitems), sms);
+        k_count_cta<PV, COL, true><<<grid, NW * 32, 0, s>>>(c, Wh, levels, heavy, lay.total);
         KC_LAUNCHED();
+        return KC_OK;
     }
-    // W = 1: one warp per owner
-    {
-        const int64_t q0 = ge_at(33), q1 = ge_at(std::max<int64_t>(1, dmin));
-        if (q1 > q0) {
-            Ctx c = base;
-            c.q0 = q0;
-            c.q1 = q1;
-            c.cursor = cursors + ci++;
-            auto kern = k_count_w1<PV, COL>;
-            const int64_t warps = q1 - q0;
-            const int grid = (int)std::min<int64_t>((warps + 7) / 8, (int64_t)sms * cc::blocks_per_sm(kern, 256, 0));
-            kern<<<grid, 256, 0, s>>>(c);
-            KC_LAUNCHED();
-        }
+    if (slot == kOwnerSlots - 1) {
+        auto kern = k_count_w1<PV, COL>;
+        const int grid = (int)std::min<int64_t>((c.nitems + 7) / 8, (int64_t)sms * cc::blocks_per_sm(kern, 256, 0));
+        kern<<<grid, 256, 0, s>>>(c);
+        KC_LAUNCHED();
+        return KC_OK;
     }
+    const int W = slot_words(slot);
+    if (dfs_reg_supported(k)) return dfs_reg_launch(c, W, PV, COL, s);  // register-resident search
+    const int NW = warps_for_width(W);
+    const Layout lay = make_layout(W, W + 1, NW, levels, PV, COL);
+    const size_t smem = (size_t)lay.total * 4;
+    auto kern = k_count_cta<PV, COL, false>;
+    if (smem > 48 * 1024) KC_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int grid = (int)std::min<int64_t>(c.nitems, (int64_t)sms * cc::blocks_per_sm(kern, NW * 32, smem));
+    kern<<<grid, NW * 32, smem, s>>>(c, W, levels, nullptr, 0);
+    KC_LAUNCHED();
     return KC_OK;
 }
 
-}  // namespace
-
-int64_t heavy_scratch_words(const kc_graph* g, int k, int64_t* slot_words)
+kc_status launch_slot(int slot, int Wh, const Ctx& c, bool pv, bool col, uint32_t* heavy, int64_t heavy_words,
+                      cudaStream_t s)
 {
-    *slot_words = 0;
-    const int64_t cut = 32LL * smem_max_words();
-    if (g->max_dplus <= cut || k - 1 > g->max_dplus) return 0;
-    const int64_t nheavy = g->ge[(size_t)std::max<int64_t>(cut + 1, k - 1)];
-    if (nheavy <= 0) return 0;
-    if (count_algo() == KC_ALGO_PIVOT) {
-        const int64_t total = sct_heavy_words(g, k, nheavy);
-        *slot_words = sct_heavy_words(g, k, 1);
-        return total;
+    if (count_algo() == KC_ALGO_PIVOT) return sct_launch_slot(slot, Wh, c, pv, col, heavy, heavy_words, s);
+    if (pv) {
+        if (col) return KC_ENOTSUP;
+        return launch_slot_dfs<true, false>(slot, Wh, c, heavy, heavy_words, s);
     }
-    const int W = (g->max_dplus + 31) / 32;
-    const int levels = k > 3 ? k - 3 : 1;
-    const Layout lay = make_layout(W, W, 8, levels, true, true);
-    const int64_t slots = std::min<int64_t>(nheavy, num_sms());
-    *slot_words = lay.total;
-    return lay.total * slots;
+    if (col) return launch_slot_dfs<false, true>(slot, Wh, c, heavy, heavy_words, s);
+    return launch_slot_dfs<false, false>(slot, Wh, c, heavy, heavy_words, s);
 }
 
-kc_status count_launch(const kc_graph* g, const CountArgs& a, unsigned long long* cursors,
-                       uint32_t* heavy_scratch, int64_t heavy_words, cudaStream_t s)
+Ctx base_ctx(const CountArgs& a)
 {
     Ctx c;
-    c.offp = g->offp;
-    c.adjp = g->adjp;
-    c.queue = g->queue;
-    c.perm = g->perm;
+    c.offp = nullptr;
+    c.adjp = nullptr;
+    c.queue = nullptr;
+    c.perm = nullptr;
     c.q0 = c.q1 = 0;
+    c.nitems = 0;
+    c.qoff = 0;
+    c.qstride = 1;
+    c.gd = nullptr;
+    c.gq0 = nullptr;
+    c.gpre = nullptr;
+    c.ng = 0;
     c.k = a.k;
     c.colours = a.colours;
     c.seed = a.seed;
@@ -549,14 +509,123 @@ kc_status count_launch(const kc_graph* g, const CountArgs& a, unsigned long long
     c.po = a.po;
     c.cursor = nullptr;
     c.work = a.work;
-    const bool col = a.colours >= 2;  // one colour keeps every pair
-    if (count_algo() == KC_ALGO_PIVOT) return sct_launch(g, a, c, cursors, heavy_scratch, heavy_words, s);
-    if (a.per_vertex) {
-        if (col) return KC_ENOTSUP;
-        return launch_classes<true, false>(g, c, cursors, heavy_scratch, heavy_words, s);
+    return c;
+}
+
+}  // namespace
+
+int slot_words(int slot)
+{
+    if (slot <= 0 || slot >= kOwnerSlots) return slot == kOwnerSlots - 1 ? 1 : 0;
+    return kClassWords[kNumSmemClasses - slot];
+}
+
+void class_range(const kc_graph* g, int k, int slot, int64_t* q0, int64_t* q1)
+{
+    auto ge_at = [&](int64_t t) -> int64_t {
+        if (t <= 0) return g->n;
+        return t <= (int64_t)g->max_dplus ? g->ge[(size_t)t] : 0;
+    };
+    const int64_t dmin = k - 1;  // Reduce 1 filter
+    const int maxw = smem_max_words();
+    *q0 = *q1 = 0;
+    if (slot == 0) {
+        *q1 = ge_at(std::max<int64_t>(32LL * maxw + 1, dmin));
+    } else if (slot == kOwnerSlots - 1) {
+        *q0 = ge_at(33);
+        *q1 = ge_at(std::max<int64_t>(1, dmin));
+    } else {
+        const int cl = kNumSmemClasses - slot;  // index into kClassWords
+        const int W = kClassWords[cl];
+        if (W > maxw) return;
+        const int64_t dlo = 32LL * kClassWords[cl - 1] + 1, dhi = 32LL * W;
+        *q0 = ge_at(dhi + 1);
+        *q1 = ge_at(std::max(dlo, dmin));
     }
-    if (col) return launch_classes<false, true>(g, c, cursors, heavy_scratch, heavy_words, s);
-    return launch_classes<false, false>(g, c, cursors, heavy_scratch, heavy_words, s);
+    if (*q1 < *q0) *q1 = *q0;
+}
+
+int64_t heavy_scratch_words_w(int W, int k, int64_t nheavy, int64_t* slot_words)
+{
+    *slot_words = 0;
+    if (nheavy <= 0) return 0;
+    if (count_algo() == KC_ALGO_PIVOT) {
+        *slot_words = sct_heavy_words_w(W, k, 1);
+        return sct_heavy_words_w(W, k, nheavy);
+    }
+    const int levels = k > 3 ? k - 3 : 1;
+    const Layout lay = make_layout(W, W, 8, levels, true, true);
+    const int64_t slots = std::min<int64_t>(nheavy, num_sms());
+    *slot_words = lay.total;
+    return lay.total * slots;
+}
+
+int64_t heavy_scratch_words(const kc_graph* g, int k, int64_t* slot_words)
+{
+    int64_t q0 = 0, q1 = 0;
+    class_range(g, k, 0, &q0, &q1);
+    return heavy_scratch_words_w((g->max_dplus + 31) / 32, k, q1 - q0, slot_words);
+}
+
+kc_status count_launch(const kc_graph* g, const CountArgs& a, unsigned long long* cursors,
+                       uint32_t* heavy_scratch, int64_t heavy_words, cudaStream_t s)
+{
+    Ctx base = base_ctx(a);
+    base.offp = g->offp;
+    base.adjp = g->adjp;
+    base.queue = g->queue;
+    base.perm = g->perm;
+    const int64_t part = a.nparts > 1 ? a.part : 0, nparts = a.nparts > 1 ? a.nparts : 1;
+    const bool col = a.colours >= 2;  // one colour keeps every pair
+    const int Wh = (g->max_dplus + 31) / 32;
+    for (int slot = 0; slot < kOwnerSlots; ++slot) {
+        Ctx c = base;
+        class_range(g, a.k, slot, &c.q0, &c.q1);
+        const int64_t span = c.q1 - c.q0;
+        c.qoff = part;
+        c.qstride = nparts;
+        c.nitems = span > part ? (span - part + nparts - 1) / nparts : 0;
+        c.cursor = cursors + slot;
+        KC_TRY(launch_slot(slot, Wh, c, a.per_vertex, col, heavy_scratch, heavy_words, s));
+    }
+    return KC_OK;
+}
+
+kc_status count_batch_launch(const kc_graph* const* gs, int ng, const CountArgs& a, const void* descs,
+                             int64_t* tables, unsigned long long* cursors, uint32_t* heavy_scratch,
+                             int64_t heavy_words, std::vector<int64_t>& host_tables, cudaStream_t s)
+{
+    Ctx base = base_ctx(a);
+    base.gd = (const cc::GraphDesc*)descs;
+    base.ng = ng;
+    const bool col = a.colours >= 2;
+    int Wh = 1;
+    for (int g = 0; g < ng; ++g) Wh = std::max(Wh, (gs[g]->max_dplus + 31) / 32);
+    // per slot: gq0[ng] then gpre[ng + 1]
+    const int64_t per = 2LL * ng + 1;
+    host_tables.assign((size_t)(per * kOwnerSlots), 0);
+    for (int slot = 0; slot < kOwnerSlots; ++slot) {
+        int64_t* hq0 = host_tables.data() + slot * per;
+        int64_t* hpre = hq0 + ng;
+        hpre[0] = 0;
+        for (int g = 0; g < ng; ++g) {
+            int64_t q0 = 0, q1 = 0;
+            class_range(gs[g], a.k, slot, &q0, &q1);
+            hq0[g] = q0;
+            hpre[g + 1] = hpre[g] + (q1 - q0);
+        }
+    }
+    KC_CK(cudaMemcpyAsync(tables, host_tables.data(), host_tables.size() * sizeof(int64_t),
+                          cudaMemcpyHostToDevice, s));
+    for (int slot = 0; slot < kOwnerSlots; ++slot) {
+        Ctx c = base;
+        c.gq0 = tables + slot * per;
+        c.gpre = c.gq0 + ng;
+        c.nitems = host_tables[(size_t)(slot * per + ng + ng)];
+        c.cursor = cursors + slot;
+        KC_TRY(launch_slot(slot, Wh, c, false, col, heavy_scratch, heavy_words, s));
+    }
+    return KC_OK;
 }
 
 }  // namespace kc

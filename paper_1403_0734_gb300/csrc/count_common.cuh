@@ -11,12 +11,31 @@
 namespace kc {
 namespace cc {
 
+// One oriented graph as the kernels see it (device pointers).
+struct GraphDesc {
+    const int64_t* offp;
+    const int32_t* adjp;
+    const int32_t* queue;
+    const int32_t* perm;
+};
+
+// Launch context of one owner class.  Single-graph mode (ng == 0): item i is
+// the owner at queue position q0 + qoff + i * qstride (qoff/qstride select a
+// part of the owners).  Batch mode (ng > 0): item i belongs to graph g with
+// gpre[g] <= i < gpre[g+1] and is the owner at position gq0[g] + i - gpre[g]
+// of that graph's queue; totals are per graph.
 struct Ctx {
     const int64_t* __restrict__ offp;
     const int32_t* __restrict__ adjp;
     const int32_t* __restrict__ queue;
     const int32_t* __restrict__ perm;
     int64_t q0, q1;
+    int64_t nitems;
+    int64_t qoff, qstride;
+    const GraphDesc* gd;
+    const int64_t* gq0;
+    const int64_t* gpre;
+    int ng;
     int k;
     uint32_t colours;
     uint64_t seed;
@@ -26,6 +45,31 @@ struct Ctx {
     unsigned long long* cursor;
     unsigned long long* work;  // nullable: bitmap word-operations executed
 };
+
+// The owner (rank r) of class item `item`, with a context whose graph
+// pointers and total are that owner's graph's.  False past the last item.
+__device__ __forceinline__ bool resolve(const Ctx& b, int64_t item, Ctx& c, int32_t& r)
+{
+    if (item >= b.nitems) return false;
+    c = b;
+    if (b.ng == 0) {
+        r = b.queue[b.q0 + b.qoff + item * b.qstride];
+        return true;
+    }
+    int lo = 0, hi = b.ng;  // largest g with gpre[g] <= item
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (b.gpre[mid] <= item) lo = mid; else hi = mid;
+    }
+    const GraphDesc gd = b.gd[lo];
+    c.offp = gd.offp;
+    c.adjp = gd.adjp;
+    c.queue = gd.queue;
+    c.perm = gd.perm;
+    c.total = b.total + 2 * lo;
+    r = gd.queue[b.gq0[lo] + (item - b.gpre[lo])];
+    return true;
+}
 
 // colour(u, x): splitmix64 output function over seed ^ (G * (u<<32 | x)),
 // reduced to [0, c) by a 64x64 multiply-high (Sec. 6; spec in kc.h).

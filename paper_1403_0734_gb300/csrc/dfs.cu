@@ -353,7 +353,7 @@ __device__ unsigned long long dfs_reg(uint32_t c0, int need0, int Wd, const uint
 }
 
 template <bool PV, bool COL>
-__global__ void __launch_bounds__(256, 4) k_dfs_reg(Ctx c, int W, int R, int clo, int chi)
+__global__ void __launch_bounds__(256, 4) k_dfs_reg(Ctx cb, int W, int R, int clo, int chi)
 {
     extern __shared__ __align__(16) uint32_t smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, NW = blockDim.x >> 5;
@@ -367,17 +367,15 @@ __global__ void __launch_bounds__(256, 4) k_dfs_reg(Ctx c, int W, int R, int clo
     __shared__ int s_next;
     __shared__ unsigned long long s_tot, s_wk;
     __shared__ long long s_item;
-    const int r0 = c.k - 1;
-    unsigned long long* wkp_dummy = nullptr;
-    (void)wkp_dummy;
+    const int r0 = cb.k - 1;
 
     for (;;) {
-        if (threadIdx.x == 0) s_item = (long long)atomicAdd(c.cursor, 1ull);
+        if (threadIdx.x == 0) s_item = (long long)atomicAdd(cb.cursor, 1ull);
         __syncthreads();
-        const int64_t q = c.q0 + s_item / R;
         const int part = (int)(s_item % R);
-        if (q >= c.q1) break;
-        const int32_t r = c.queue[q];
+        Ctx c;
+        int32_t r;
+        if (!cc::resolve(cb, (int64_t)(s_item / R), c, r)) break;
         const int64_t b = c.offp[r];
         const int d = (int)(c.offp[r + 1] - b);
         const int Wd = (d + 31) >> 5;
@@ -490,7 +488,7 @@ kc_status dfs_reg_launch(const cc::Ctx& c, int W, bool pv, bool col, cudaStream_
         if (smem > 48 * 1024)
             KC_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         const int grid =
-            (int)std::min<int64_t>((c.q1 - c.q0) * R, (int64_t)sms * cc::blocks_per_sm(kern, NW * 32, smem));
+            (int)std::min<int64_t>(c.nitems * R, (int64_t)sms * cc::blocks_per_sm(kern, NW * 32, smem));
         kern<<<grid, NW * 32, smem, s>>>(c, W, R, g_compact_lo, g_compact_hi);
         KC_LAUNCHED();
         return KC_OK;

@@ -48,7 +48,10 @@ constexpr uint32_t kFull = 0xffffffffu;
 // G+(u).  Class c covers d+ in (32*W(c-1), 32*W(c)].
 constexpr int kNumSmemClasses = 6;               // W = 1, 2, 4, 8, 16, 32
 constexpr int kClassWords[kNumSmemClasses] = {1, 2, 4, 8, 16, 32};
-constexpr int kSmemMaxD = 32 * 32;               // 1024: larger owners use global tiles
+// Owner slots in launch order: 0 = rows wider than the shared-memory limit
+// (global tiles), 1..5 = shared-memory rows of 32, 16, 8, 4, 2 words,
+// 6 = one word (registers).
+constexpr int kOwnerSlots = 7;
 
 // ---------------------------------------------------------- graph handle
 
@@ -103,10 +106,25 @@ struct CountArgs {
     unsigned long long* pv;     // [n] rank space, nullable
     unsigned long long* po;     // [n] rank space, nullable
     unsigned long long* work;   // [1] bitmap word-operations executed, nullable
+    int part = 0, nparts = 1;   // count only owners at queue positions = part (mod nparts)
 };
 
+// cursors: kOwnerSlots zeroed counters.
 kc_status count_launch(const kc_graph* g, const CountArgs& a, unsigned long long* cursors,
                        uint32_t* heavy_scratch, int64_t heavy_words, cudaStream_t s);
+
+// One launch sequence over the owners of ng graphs.  descs: device array of
+// ng graph descriptors; tables: device scratch of kOwnerSlots * (2 ng + 1)
+// int64; a.total: 2 words per graph; host_tables must stay alive until the
+// stream has consumed it.
+kc_status count_batch_launch(const kc_graph* const* gs, int ng, const CountArgs& a, const void* descs,
+                             int64_t* tables, unsigned long long* cursors, uint32_t* heavy_scratch,
+                             int64_t heavy_words, std::vector<int64_t>& host_tables, cudaStream_t s);
+
+// Queue range of owner slot `slot` for k under the current knobs.
+void class_range(const kc_graph* g, int k, int slot, int64_t* q0, int64_t* q1);
+int slot_words(int slot);
+int64_t heavy_scratch_words_w(int W, int k, int64_t nheavy, int64_t* slot_words);
 
 extern bool g_work_enabled;
 extern unsigned long long g_last_work;

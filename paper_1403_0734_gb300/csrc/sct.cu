@@ -32,6 +32,7 @@ namespace kc {
 
 int num_sms();
 int smem_max_words();
+int slot_words(int slot);
 
 namespace {
 
@@ -58,17 +59,17 @@ __device__ __forceinline__ unsigned long long binom(int n, int r, bool* ovf)
 // ------------------------------------------------------------ W = 1 class
 
 template <bool PV, bool COL>
-__global__ void __launch_bounds__(256) k_sct_w1(Ctx c)
+__global__ void __launch_bounds__(256) k_sct_w1(Ctx cb)
 {
     const int lane = threadIdx.x & 31;
-    const int need = c.k - 1;  // clique vertices inside G+(u)
+    const int need = cb.k - 1;  // clique vertices inside G+(u)
     for (;;) {
         unsigned long long pos = 0;
-        if (lane == 0) pos = atomicAdd(c.cursor, 1ull);
+        if (lane == 0) pos = atomicAdd(cb.cursor, 1ull);
         pos = __shfl_sync(kFull, pos, 0);
-        const int64_t q = c.q0 + (int64_t)pos;
-        if (q >= c.q1) break;
-        const int32_t r = c.queue[q];
+        Ctx c;
+        int32_t r;
+        if (!cc::resolve(cb, (int64_t)pos, c, r)) break;
         const int64_t b = c.offp[r];
         const int d = (int)(c.offp[r + 1] - b);
         const int32_t x = lane < d ? c.adjp[b + lane] : INT_MAX;
@@ -218,11 +219,11 @@ __host__ __device__ inline WLayout make_wlayout(int W, int RS, int need, bool pv
 }
 
 template <bool PV, bool COL, bool HEAVY>
-__global__ void __launch_bounds__(256) k_sct_warp(Ctx c, int W, uint32_t* gscratch, int64_t slot_words)
+__global__ void __launch_bounds__(256) k_sct_warp(Ctx cb, int W, uint32_t* gscratch, int64_t slot_words)
 {
     extern __shared__ __align__(16) uint32_t smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int need = c.k - 1;
+    const int need = cb.k - 1;
     const int RS = HEAVY ? W : W + 1;
     const WLayout lay = make_wlayout(W, RS, need, PV, COL);
     uint32_t* base = HEAVY ? gscratch + ((int64_t)blockIdx.x * (blockDim.x >> 5) + wid) * slot_words
@@ -239,11 +240,11 @@ __global__ void __launch_bounds__(256) k_sct_warp(Ctx c, int W, uint32_t* gscrat
 
     for (;;) {
         unsigned long long pos = 0;
-        if (lane == 0) pos = atomicAdd(c.cursor, 1ull);
+        if (lane == 0) pos = atomicAdd(cb.cursor, 1ull);
         pos = __shfl_sync(kFull, pos, 0);
-        const int64_t q = c.q0 + (int64_t)pos;
-        if (q >= c.q1) break;
-        const int32_t r = c.queue[q];
+        Ctx c;
+        int32_t r;
+        if (!cc::resolve(cb, (int64_t)pos, c, r)) break;
         const int64_t b = c.offp[r];
         const int d = (int)(c.offp[r + 1] - b);
         const int Wd = (d + 31) >> 5;
@@ -468,97 +469,61 @@ __global__ void __launch_bounds__(256) k_sct_warp(Ctx c, int W, uint32_t* gscrat
 }
 
 template <bool PV, bool COL>
-kc_status launch_sct(const kc_graph* g, Ctx base, unsigned long long* cursors, uint32_t* heavy,
-                     int64_t heavy_words, cudaStream_t s)
+kc_status launch_slot_sct(int slot, int Wh, const Ctx& c, uint32_t* heavy, int64_t heavy_words, cudaStream_t s)
 {
+    if (c.nitems <= 0) return KC_OK;
     const int sms = num_sms();
-    const int k = base.k;
-    const int need = k - 1;
-    auto ge_at = [&](int64_t t) -> int64_t {
-        if (t <= 0) return g->n;
-        return t <= (int64_t)g->max_dplus ? g->ge[(size_t)t] : 0;
-    };
-    const int64_t dmin = k - 1;
-    const int maxw = smem_max_words();
-    int ci = 0;
-
-    // owners wider than the shared-memory limit: one warp each, global tiles
-    {
-        const int64_t q1 = ge_at(std::max<int64_t>(32LL * maxw + 1, dmin)), q0 = 0;
-        if (q1 > q0) {
-            const int W = (g->max_dplus + 31) / 32;
-            const WLayout lay = make_wlayout(W, W, need, PV, COL);
-            const int64_t slots = heavy_words / lay.total;
-            if (slots < 1) return KC_ENOMEM;
-            const int NW = (int)std::min<int64_t>(4, slots);
-            Ctx c = base;
-            c.q0 = q0;
-            c.q1 = q1;
-            c.cursor = cursors + ci++;
-            const int64_t warps = std::min<int64_t>(slots, q1 - q0);
-            const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(warps / NW, (int64_t)sms * 8));
-            k_sct_warp<PV, COL, true><<<grid, NW * 32, 0, s>>>(c, W, heavy, lay.total);
-            KC_LAUNCHED();
-        }
-    }
-    for (int cl = kNumSmemClasses - 1; cl >= 1; --cl) {
-        const int W = kClassWords[cl];
-        if (W > maxw) continue;
-        const int64_t dlo = 32LL * kClassWords[cl - 1] + 1, dhi = 32LL * W;
-        const int64_t q0 = ge_at(dhi + 1), q1 = ge_at(std::max(dlo, dmin));
-        if (q1 <= q0) continue;
-        const WLayout lay = make_wlayout(W, W + 1, need, PV, COL);
-        const size_t per_warp = (size_t)lay.total * 4;
-        int NW = (int)std::max<size_t>(1, std::min<size_t>(8, (size_t)(100 * 1024) / per_warp));
-        const size_t smem = per_warp * NW;
-        auto kern = k_sct_warp<PV, COL, false>;
-        if (smem > 48 * 1024) KC_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        Ctx c = base;
-        c.q0 = q0;
-        c.q1 = q1;
-        c.cursor = cursors + ci++;
-        const int64_t ctas = (q1 - q0 + NW - 1) / NW;
-        const int grid = (int)std::min<int64_t>(ctas, (int64_t)sms * cc::blocks_per_sm(kern, NW * 32, smem));
-        kern<<<grid, NW * 32, smem, s>>>(c, W, nullptr, 0);
+    const int need = c.k - 1;
+    if (slot == 0) {  // rows wider than the shared-memory limit: global tiles, one warp each
+        const WLayout lay = make_wlayout(Wh, Wh, need, PV, COL);
+        const int64_t slots = heavy_words / lay.total;
+        if (slots < 1) return KC_ENOMEM;
+        const int NW = (int)std::min<int64_t>(4, slots);
+        const int64_t warps = std::min<int64_t>(slots, c.nitems);
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(warps / NW, (int64_t)sms * 8));
+        k_sct_warp<PV, COL, true><<<grid, NW * 32, 0, s>>>(c, Wh, heavy, lay.total);
         KC_LAUNCHED();
+        return KC_OK;
     }
-    {
-        const int64_t q0 = ge_at(33), q1 = ge_at(std::max<int64_t>(1, dmin));
-        if (q1 > q0) {
-            Ctx c = base;
-            c.q0 = q0;
-            c.q1 = q1;
-            c.cursor = cursors + ci++;
-            auto kern = k_sct_w1<PV, COL>;
-            const int64_t warps = q1 - q0;
-            const int grid = (int)std::min<int64_t>((warps + 7) / 8, (int64_t)sms * cc::blocks_per_sm(kern, 256, 0));
-            kern<<<grid, 256, 0, s>>>(c);
-            KC_LAUNCHED();
-        }
+    if (slot == kOwnerSlots - 1) {
+        auto kern = k_sct_w1<PV, COL>;
+        const int grid = (int)std::min<int64_t>((c.nitems + 7) / 8, (int64_t)sms * cc::blocks_per_sm(kern, 256, 0));
+        kern<<<grid, 256, 0, s>>>(c);
+        KC_LAUNCHED();
+        return KC_OK;
     }
+    const int W = slot_words(slot);
+    const WLayout lay = make_wlayout(W, W + 1, need, PV, COL);
+    const size_t per_warp = (size_t)lay.total * 4;
+    const int NW = (int)std::max<size_t>(1, std::min<size_t>(8, (size_t)(100 * 1024) / per_warp));
+    const size_t smem = per_warp * NW;
+    auto kern = k_sct_warp<PV, COL, false>;
+    if (smem > 48 * 1024) KC_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int64_t ctas = (c.nitems + NW - 1) / NW;
+    const int grid = (int)std::min<int64_t>(ctas, (int64_t)sms * cc::blocks_per_sm(kern, NW * 32, smem));
+    kern<<<grid, NW * 32, smem, s>>>(c, W, nullptr, 0);
+    KC_LAUNCHED();
     return KC_OK;
 }
 
 }  // namespace
 
-int64_t sct_heavy_words(const kc_graph* g, int k, int64_t nheavy)
+int64_t sct_heavy_words_w(int W, int k, int64_t nheavy)
 {
-    const int W = (g->max_dplus + 31) / 32;
     const WLayout lay = make_wlayout(W, W, k - 1, true, true);
     const int64_t slots = std::min<int64_t>(nheavy, (int64_t)num_sms() * 4);
     return lay.total * slots;
 }
 
-kc_status sct_launch(const kc_graph* g, const CountArgs& a, const cc::Ctx& c, unsigned long long* cursors,
-                     uint32_t* heavy, int64_t heavy_words, cudaStream_t s)
+kc_status sct_launch_slot(int slot, int Wh, const cc::Ctx& c, bool pv, bool col, uint32_t* heavy,
+                          int64_t heavy_words, cudaStream_t s)
 {
-    const bool col = a.colours >= 2;
-    if (a.per_vertex) {
+    if (pv) {
         if (col) return KC_ENOTSUP;
-        return launch_sct<true, false>(g, c, cursors, heavy, heavy_words, s);
+        return launch_slot_sct<true, false>(slot, Wh, c, heavy, heavy_words, s);
     }
-    if (col) return launch_sct<false, true>(g, c, cursors, heavy, heavy_words, s);
-    return launch_sct<false, false>(g, c, cursors, heavy, heavy_words, s);
+    if (col) return launch_slot_sct<false, true>(slot, Wh, c, heavy, heavy_words, s);
+    return launch_slot_sct<false, false>(slot, Wh, c, heavy, heavy_words, s);
 }
 
 }  // namespace kc

@@ -82,6 +82,12 @@ def _load():
     lib.kc_estimate_csr.argtypes = [_P, _P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int, ctypes.c_uint32,
                                     ctypes.c_uint64, ctypes.c_uint, _P, _P, _P]
     lib.kc_estimate_csr.restype = st
+    lib.kc_footprint.argtypes = [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]
+    lib.kc_footprint.restype = st
+    lib.kc_count_part.argtypes = [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint, _P, _P, _P, _P]
+    lib.kc_count_part.restype = st
+    lib.kc_count_batch.argtypes = [_P, ctypes.c_int, ctypes.c_int, ctypes.c_uint, _P, _P]
+    lib.kc_count_batch.restype = st
     lib.kc_count_static.argtypes = [_P, ctypes.c_int, ctypes.c_uint, _P, _P]
     lib.kc_count_static.restype = st
     lib.kc_set_param.argtypes = [ctypes.c_int, ctypes.c_int64]
@@ -227,6 +233,36 @@ def count(g: Graph, k: int, per_vertex: bool = False, per_owner: bool = False, s
     _check(_load().kc_count(g.handle, k, 0, ctypes.byref(tot), _ptr(pv), _ptr(po), _stream_handle(stream)),
            f"kc_count(k={k})")
     return int(tot.value), (pv[: g.n] if pv is not None else None), (po[: g.n] if po is not None else None)
+
+
+def footprint(g: Graph, k: int, per_vertex: bool = False, per_owner: bool = False,
+              host_outputs: bool = True) -> int:
+    """Device bytes a count/estimate call allocates while it runs (kc_footprint)."""
+    b = ctypes.c_uint64(0)
+    _check(_load().kc_footprint(g.handle, k, int(per_vertex), int(per_owner), int(host_outputs), ctypes.byref(b)),
+           "kc_footprint")
+    return int(b.value)
+
+
+def count_part(g: Graph, k: int, part: int, nparts: int, per_vertex: bool = False, per_owner: bool = False,
+               stream=None):
+    """The share of FFF_k counted by owners part, part+nparts, ... of the work
+    queue (kc_count_part).  Summing the parts gives count()."""
+    pv = np.empty(max(g.n, 1), np.uint64) if per_vertex else None
+    po = np.empty(max(g.n, 1), np.uint64) if per_owner else None
+    tot = ctypes.c_uint64(0)
+    _check(_load().kc_count_part(g.handle, k, part, nparts, 0, ctypes.byref(tot), _ptr(pv), _ptr(po),
+                                 _stream_handle(stream)), f"kc_count_part(k={k}, {part}/{nparts})")
+    return int(tot.value), (pv[: g.n] if pv is not None else None), (po[: g.n] if po is not None else None)
+
+
+def count_batch(graphs, k: int, stream=None):
+    """q_k of every graph in one launch sequence (kc_count_batch)."""
+    hs = (_P * max(len(graphs), 1))(*[gr.handle for gr in graphs])
+    out = np.zeros(max(len(graphs), 1), np.uint64)
+    _check(_load().kc_count_batch(hs, len(graphs), k, 0, out.ctypes.data, _stream_handle(stream)),
+           f"kc_count_batch(k={k})")
+    return [int(x) for x in out[: len(graphs)]]
 
 
 def count_device(g: Graph, k: int, total, per_vertex=None, per_owner=None, stream=None):

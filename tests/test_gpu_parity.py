@@ -295,3 +295,60 @@ def test_repeatable(kc):
     a = kc.count(G, 5, per_vertex=True)
     b = kc.count(G, 5, per_vertex=True)
     assert a[0] == b[0] and np.array_equal(a[1], b[1])
+
+
+# ------------------------------------------------------------ parts and batches
+
+@pytest.mark.parametrize("maxw", [32, 1])
+def test_parts_add_up_to_the_count(kc, maxw):
+    kc.set_param(kc.KC_PARAM_SMEM_MAX_WORDS, maxw)
+    try:
+        g = graph("rmat_s14")
+        G = kc.orient(g.off, g.adj)
+        for k in (3, 4, 5):
+            t, pv, po = kc.count(G, k, per_vertex=True, per_owner=True)
+            for nparts in (2, 3, 7):
+                parts = [kc.count_part(G, k, p, nparts, per_vertex=True, per_owner=True) for p in range(nparts)]
+                assert sum(x[0] for x in parts) == t
+                spv = np.zeros(g.n, np.uint64)
+                spo = np.zeros(g.n, np.uint64)
+                owners = np.zeros(g.n, np.int64)
+                for x in parts:
+                    spv += x[1]
+                    spo += x[2]
+                    owners += (x[2] > 0)
+                assert np.array_equal(spv, pv) and np.array_equal(spo, po)
+                assert owners.max() <= 1  # every owner counted by one part
+    finally:
+        kc.set_param(kc.KC_PARAM_SMEM_MAX_WORDS, 32)
+
+
+def test_part_arguments(kc):
+    g = graph("er_1000")
+    G = kc.orient(g.off, g.adj)
+    for bad in ((3, 0, 0), (3, 2, 2), (3, -1, 2), (2, 0, 2)):
+        with pytest.raises(kc.KcError):
+            kc.count_part(G, bad[0], bad[1], bad[2])
+
+
+@pytest.mark.parametrize("maxw", [32, 1])
+def test_batch_matches_solo_counts(kc, maxw):
+    graphs = kcgen.batch_workload(48, seed=3, nmin=20, nmax=4000)
+    Gs = [kc.orient(g.off, g.adj) for g in graphs]
+    kc.set_param(kc.KC_PARAM_SMEM_MAX_WORDS, maxw)
+    try:
+        for k in (1, 2, 3, 4, 5):
+            batch = kc.count_batch(Gs, k)
+            solo = [kc.count(G, k)[0] for G in Gs]
+            assert batch == solo, k
+        for i in (0, 7, 31):
+            assert kc.count_batch(Gs, 4)[i] == oracle.count(graphs[i], 4)[0]
+    finally:
+        kc.set_param(kc.KC_PARAM_SMEM_MAX_WORDS, 32)
+
+
+def test_batch_edge_cases(kc):
+    assert kc.count_batch([], 4) == []
+    G = kc.orient(np.zeros(1, np.int64), np.zeros(0, np.int32))
+    H = kc.orient(kcgen.complete(40).off, kcgen.complete(40).adj)
+    assert kc.count_batch([G, H, G], 5) == [0, comb(40, 5), 0]

@@ -1,0 +1,79 @@
+"""Host logic of the continuous-batching server (no GPU): a fake backend that
+sleeps and returns oracle counts stands in for the C-ABI call."""
+import threading
+import time
+
+import pytest
+
+import kcgen
+import oracle
+from paper_1403_0734_gb300 import serve
+
+
+@pytest.fixture(scope="module")
+def graphs():
+    return [kcgen.random_small(22, 0.5, s) for s in range(4)]
+
+
+def make_backend(graphs, delay, tracker):
+    lock = threading.Lock()
+
+    def backend(req, stream):
+        with lock:
+            tracker["running"] += 1
+            tracker["peak"] = max(tracker["peak"], tracker["running"])
+        time.sleep(delay)
+        g = graphs[req.graph]
+        if req.colours:
+            s, est, _ = oracle.estimate(g, req.k, req.colours, req.seed)
+            out = (s, est)
+        else:
+            q = oracle.count(g, req.k)[0]
+            out = (q, float(q))
+        with lock:
+            tracker["running"] -= 1
+        return out
+    return backend
+
+
+def expected(graphs, r):
+    if r.colours:
+        return oracle.estimate(graphs[r.graph], r.k, r.colours, r.seed)[0]
+    return oracle.count(graphs[r.graph], r.k)[0]
+
+
+def test_results_and_overlap(graphs):
+    reqs = serve.poisson_stream(40, rate=400.0, ngraphs=len(graphs), seed=3)
+    tr = {"running": 0, "peak": 0}
+    srv = serve.Server(graphs, slots=4, backend=make_backend(graphs, 0.01, tr), footprint=lambda r: 100)
+    res, makespan = srv.run(reqs)
+    assert [r.rid for r in res] == list(range(40))
+    for r, q in zip(res, sorted(reqs, key=lambda x: x.rid)):
+        assert r.value == expected(graphs, q)
+        assert r.start >= q.arrival - 1e-6 and r.end >= r.start
+    assert tr["peak"] > 1  # admitted while others were still running
+    st = serve.latency_stats(res)
+    assert 0 < st["p50_ms"] <= st["p99_ms"]
+
+
+def test_budget_limits_concurrency(graphs):
+    reqs = serve.poisson_stream(16, rate=1000.0, ngraphs=len(graphs), seed=4)
+    tr = {"running": 0, "peak": 0}
+    # budget of one request at a time, although four slots are free
+    srv = serve.Server(graphs, slots=4, budget_bytes=100, backend=make_backend(graphs, 0.005, tr),
+                       footprint=lambda r: 100)
+    res, _ = srv.run(reqs)
+    assert tr["peak"] == 1 and srv.max_concurrent == 1
+    assert all(r.value == expected(graphs, q) for r, q in zip(res, sorted(reqs, key=lambda x: x.rid)))
+    # two at a time
+    tr = {"running": 0, "peak": 0}
+    srv = serve.Server(graphs, slots=4, budget_bytes=250, backend=make_backend(graphs, 0.005, tr),
+                       footprint=lambda r: 100)
+    srv.run(reqs)
+    assert tr["peak"] <= 2
+
+
+def test_oversized_request_rejected(graphs):
+    srv = serve.Server(graphs, slots=2, budget_bytes=10, backend=lambda r, s: (0, 0.0), footprint=lambda r: 11)
+    with pytest.raises(ValueError):
+        srv.run(serve.poisson_stream(2, 10.0, len(graphs), 1))
