@@ -49,6 +49,14 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["kc", "reference"], default="kc")
     ap.add_argument("--ks", default="3,4,5,6")
+    ap.add_argument("--config", choices=["chunglu", "sbm", "batch", "serving"], default="chunglu",
+                    help="chunglu: the benchmark line; sbm / batch / serving: the other workloads")
+    ap.add_argument("--batch-graphs", type=int, default=8192)
+    ap.add_argument("--serve-requests", type=int, default=1000)
+    ap.add_argument("--serve-graphs", type=int, default=64)
+    ap.add_argument("--serve-scales", default="14,18")
+    ap.add_argument("--serve-load", type=float, default=0.8,
+                    help="arrival rate as a fraction of the measured saturation throughput")
     ap.add_argument("--algo", choices=["dfs", "pivot"], default="dfs",
                     help="Reduce 3 counter (ordered DFS or pivoting clique tree)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -194,11 +202,142 @@ def run_reference(args, ks):
 
 # ------------------------------------------------------------------ GPU side
 
+def _gen(spec):
+    import kcgen
+    kind, a = spec
+    return getattr(kcgen, kind)(*a)
+
+
+def generate(specs, workers=None):
+    """Generate graphs in a spawn process pool (before any CUDA call)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    workers = workers or min(16, os.cpu_count() or 1)
+    with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(_gen, specs, chunksize=max(1, len(specs) // (4 * workers))))
+
+
+def run_sbm(args):
+    """SBM workload: exact counts k = 4..7 and cFFF_k relative error over 32
+    seeds for c in {4, 8, 16}; also the dense-block variant (p_in = 1)."""
+    import numpy as np
+    import torch
+    import kcgen
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1403_0734_gb300 as kc
+    out = {"config": "sbm", "metric": METRIC, "unit": UNIT, "variants": []}
+    for p_in in (0.3, 1.0):
+        g = kcgen.sbm_2m(1, p_in)
+        torch.cuda.synchronize()
+        G = kc.orient(torch.from_numpy(g.off).cuda(), torch.from_numpy(g.adj).cuda())
+        var = {"p_in": p_in, "n": g.n, "m": g.m, "exact": {}, "estimate": {}}
+        for k in (4, 5, 6, 7):
+            kc.count(G, k)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            q = kc.count(G, k)[0]
+            dt = time.perf_counter() - t0
+            var["exact"][str(k)] = {"q": q, "ms": dt * 1e3, "cliques_per_s": q / dt}
+            for c in (4, 8, 16):
+                ests, ts = [], []
+                for seed in range(1, 33):
+                    t0 = time.perf_counter()
+                    ests.append(kc.estimate(G, k, c, seed)[1])
+                    ts.append(time.perf_counter() - t0)
+                e = np.array(ests)
+                rel = np.abs(e - q) / q if q else np.zeros_like(e)
+                var["estimate"][f"{k},{c}"] = {
+                    "mean_estimate": float(e.mean()), "rel_err_mean": float(rel.mean()) if q else None,
+                    "rel_err_of_mean": float(abs(e.mean() - q) / q) if q else None,
+                    "rel_std": float(e.std(ddof=1) / q) if q else None, "ms": 1e3 * float(np.mean(ts)),
+                    "speedup_vs_exact": dt / float(np.mean(ts))}
+        out["variants"].append(var)
+        G.free()
+    print(json.dumps(out))
+    return 0
+
+
+def run_batch(args):
+    """Batched workload: uneven Chung-Lu graphs (n log-uniform in [50, 20000],
+    exponent 2.3, average degree in [8, 64]) counted for k = 4 in one launch
+    sequence, against one call per graph."""
+    import kcgen
+    import torch
+    specs = [("chung_lu", (n, m, 2.3, w, s)) for (n, m, w, s) in kcgen.batch_params(args.batch_graphs, 1)]
+    t0 = time.perf_counter()
+    graphs = generate(specs)
+    gen_s = time.perf_counter() - t0
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1403_0734_gb300 as kc
+    torch.cuda.init()
+    Gs = [kc.orient(g.off, g.adj) for g in graphs]
+    edges = sum(g.m for g in graphs)
+    k = 4
+    kc.count_batch(Gs, k)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tb = kc.count_batch(Gs, k)
+    batch_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    ts = [kc.count(G, k)[0] for G in Gs]
+    single_s = time.perf_counter() - t0
+    assert tb == ts
+    q = sum(tb)
+    print(json.dumps({"config": "batch", "graphs": len(Gs), "edges": edges, "k": k, "q_total": q,
+                      "batched": {"s": batch_s, "graphs_per_s": len(Gs) / batch_s, "cliques_per_s": q / batch_s,
+                                  "edges_per_s": edges / batch_s},
+                      "one_call_per_graph": {"s": single_s, "graphs_per_s": len(Gs) / single_s,
+                                             "cliques_per_s": q / single_s, "edges_per_s": edges / single_s},
+                      "speedup": single_s / batch_s, "generation_s": gen_s}))
+    return 0
+
+
+def run_serving(args):
+    """Serving: Poisson stream over device-resident R-MAT graphs (edge factor
+    16, a/b/c = .57/.19/.19), each request exact k in [3, 6] or cFFF_k with c
+    in [2, 16]; admission by device footprint; p50/p99 latency."""
+    import numpy as np
+    import torch
+    lo, hi = (int(x) for x in args.serve_scales.split(","))
+    rng = np.random.default_rng(5)
+    scales = [int(rng.integers(lo, hi + 1)) for _ in range(args.serve_graphs)]
+    graphs = generate([("rmat", (s, 16, 0.57, 0.19, 0.19, 100 + i)) for i, s in enumerate(scales)])
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1403_0734_gb300 as kc
+    from paper_1403_0734_gb300 import serve
+    torch.cuda.init()
+    Gs = [kc.orient(g.off, g.adj) for g in graphs]
+    # saturation throughput: a burst with every request present at time 0
+    probe = serve.poisson_stream(min(200, args.serve_requests), 0.0, len(Gs), seed=11)
+    srv = serve.Server(Gs, slots=8)
+    res, span = srv.run(probe, stream_factory=torch.cuda.Stream, realtime=False)
+    sat = len(probe) / span
+    reqs = serve.poisson_stream(args.serve_requests, args.serve_load * sat, len(Gs), seed=12)
+    srv = serve.Server(Gs, slots=8)
+    res, span = srv.run(reqs, stream_factory=torch.cuda.Stream)
+    st = serve.latency_stats(res)
+    exact = sum(r.value for r, q in zip(res, sorted(reqs, key=lambda x: x.rid)) if q.colours == 0)
+    print(json.dumps({"config": "serving", "graphs": len(Gs), "scales": [lo, hi], "requests": len(reqs),
+                      "saturation_req_per_s": sat, "offered_req_per_s": args.serve_load * sat,
+                      "req_per_s": len(reqs) / span, "exact_cliques_per_s": exact / span,
+                      "max_concurrent": srv.max_concurrent, **st}))
+    return 0
+
+
 def main():
     args = parse()
     ks = [int(x) for x in args.ks.split(",")]
     if args.impl == "reference":
         return run_reference(args, ks)
+    if args.config == "sbm":
+        return run_sbm(args)
+    if args.config == "batch":
+        return run_batch(args)
+    if args.config == "serving":
+        return run_serving(args)
 
     import numpy as np
     import torch
