@@ -24,6 +24,7 @@
 // neighbour-keyed counting of heavy G+(u) proposed in Sec. 7 -- so that the
 // largest owners do not leave the rest of the GPU idle at the end.
 #include <algorithm>
+#include <type_traits>
 
 #include "count_common.cuh"
 
@@ -38,6 +39,7 @@ using cc::colour_of;
 using cc::Ctx;
 using cc::mask_above;
 using cc::mask_below;
+using cc::warp_sum64;
 
 constexpr int kMaxLev = 5;  // register stack levels: k - 3 <= 5, i.e. k <= 8
 
@@ -62,7 +64,7 @@ struct RLayout {
     int64_t L, col, pvlo, pvhi, A, total;
 };
 
-__host__ __device__ inline RLayout make_rlayout(int W, int RS, bool pv, bool col)
+__host__ __device__ inline RLayout make_rlayout(int W, int RS, bool pv, bool col, int NW = 0)
 {
     const int64_t D = 32LL * W;
     RLayout l;
@@ -72,8 +74,14 @@ __host__ __device__ inline RLayout make_rlayout(int W, int RS, bool pv, bool col
     l.pvhi = l.pvlo + (pv ? D : 0);
     l.A = l.pvhi + (pv ? D : 0);
     l.total = l.A + D * RS;
+    (void)NW;
     return l;
 }
+
+// Row stride: W + 1 words (odd, conflict-free) for the generic path; a
+// multiple of 4 words (W + 4) for the 128-bit loads of the width-templated
+// path, which also staggers rows across banks.
+__host__ __device__ inline int row_stride(int W, int WM) { return WM >= 4 ? W + 4 : (WM > 0 ? 4 : W + 1); }
 
 // 64-bit membership increment as 32-bit shared atomics with a carry word.
 __device__ __forceinline__ void pv_add(uint32_t* lo, uint32_t* hi, int e, unsigned long long v)
@@ -150,6 +158,157 @@ __device__ __forceinline__ uint32_t leaf2_reg(uint32_t C, int w0, int Wd, const 
     }
     const uint32_t E = __reduce_add_sync(kFull, S);
     return PV ? E / 2u : E;
+}
+
+// Same count as leaf2_reg, for rows of at most WM words: the candidate set
+// is first copied into every lane's registers (WM broadcast shuffles), so
+// each lane runs through its element's whole row alone with 128-bit shared
+// loads and no shuffle in the loop.  Row stride RS is a multiple of 4 words.
+template <bool PV, int WM>
+__device__ __forceinline__ uint32_t leaf2_rep(uint32_t C, int Wd, const uint32_t* A, int RS, uint32_t* pvlo,
+                                              uint32_t* pvhi, int lane, unsigned long long* wk)
+{
+    uint32_t Cr[WM];
+#pragma unroll
+    for (int w = 0; w < WM; ++w) Cr[w] = __shfl_sync(kFull, C, w);
+    const uint32_t pc = (uint32_t)__popc(C);
+    uint32_t pre = pc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(kFull, pre, o);
+        if (lane >= o) pre += t;
+    }
+    const uint32_t total = __shfl_sync(kFull, pre, 31);
+    const uint32_t excl = pre - pc;
+    uint32_t S = 0;
+    for (uint32_t base = 0; base < total; base += 32) {
+        const uint32_t j = base + (uint32_t)lane;
+        int w = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            const uint32_t pv_ = __shfl_sync(kFull, pre, w + step - 1);
+            if (pv_ <= j) w += step;
+        }
+        const uint32_t cw = __shfl_sync(kFull, C, w);
+        const uint32_t ex = __shfl_sync(kFull, excl, w);
+        if (j < total) {
+            const int e = w * 32 + (int)__fns(cw, 0, (int)(j - ex) + 1);
+            uint32_t f = 0;
+            if (WM >= 4) {
+                const uint4* A4 = (const uint4*)(A + (int64_t)e * RS);
+#pragma unroll
+                for (int q = 0; q < WM / 4; ++q) {
+                    const uint4 a = A4[q];
+                    f += (uint32_t)(__popc(Cr[4 * q] & a.x) + __popc(Cr[4 * q + 1] & a.y) +
+                                    __popc(Cr[4 * q + 2] & a.z) + __popc(Cr[4 * q + 3] & a.w));
+                }
+            } else {
+                const uint32_t* Ae = A + (int64_t)e * RS;
+#pragma unroll
+                for (int q = 0; q < WM; ++q) f += (uint32_t)__popc(Cr[q] & Ae[q]);
+            }
+            S += f;
+            if (PV && f) pv_add(pvlo, pvhi, e, f);
+        }
+        if (wk) *wk += (unsigned long long)__reduce_add_sync(kFull, j < total ? (unsigned)Wd : 0u);
+    }
+    const uint32_t E = __reduce_add_sync(kFull, S);
+    return PV ? E / 2u : E;
+}
+
+// Last level for a class of row width WM (0: generic loop).
+template <bool PV, int WM>
+__device__ __forceinline__ uint32_t leaf2_any(uint32_t C, int w0, int Wd, const uint32_t* A, int RS, uint32_t* pvlo,
+                                              uint32_t* pvhi, int lane, unsigned long long* wk)
+{
+    if (WM > 0) return leaf2_rep<PV, (WM > 0 ? WM : 1)>(C, Wd, A, RS, pvlo, pvhi, lane, wk);
+    return leaf2_reg<PV>(C, w0, Wd, A, RS, pvlo, pvhi, lane, wk);
+}
+
+// All children of a node whose candidate set C (lane w holds word w) still
+// needs three vertices: the cliques below are the triangles of G[C].
+// Without memberships each lane takes one child e of C, forms Ce = C & N(e)
+// above e in its own registers and counts the edges inside Ce by walking
+// Ce's elements itself (128-bit row loads, no shuffles).  With memberships
+// (symmetric rows) each lane takes one element f of C instead and counts the
+// edges inside N(f) & C -- the triangles of G[C] through f, f's membership
+// increment -- so no lane writes another lane's counter; the number of
+// triangles is a third of their sum.  sC: per-warp buffer of WM words
+// (16-byte aligned).
+template <bool PV, int WM>
+__device__ unsigned long long penult3(uint32_t C, int Wd, const uint32_t* A, int RS, uint32_t* pvlo,
+                                      uint32_t* pvhi, uint32_t* sC, int lane, unsigned long long* wk)
+{
+    if (lane < WM) sC[lane] = C;
+    __syncwarp();
+    const uint32_t pc = (uint32_t)__popc(C);
+    uint32_t pre = pc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(kFull, pre, o);
+        if (lane >= o) pre += t;
+    }
+    const uint32_t total = __shfl_sync(kFull, pre, 31);
+    const uint32_t excl = pre - pc;
+    unsigned long long tot = 0, wl = 0;
+    for (uint32_t base = 0; base < total; base += 32) {
+        const uint32_t j = base + (uint32_t)lane;
+        int w = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            const uint32_t pv_ = __shfl_sync(kFull, pre, w + step - 1);
+            if (pv_ <= j) w += step;
+        }
+        const uint32_t cw = __shfl_sync(kFull, C, w);
+        const uint32_t ex = __shfl_sync(kFull, excl, w);
+        if (j < total) {
+            const int e = w * 32 + (int)__fns(cw, 0, (int)(j - ex) + 1);
+            // Ce = C & N(e): with upper rows the elements above e, with
+            // symmetric rows all neighbours of e in C
+            uint32_t Ce[WM];
+            const uint4* Ae4 = (const uint4*)(A + (int64_t)e * RS);
+            const uint4* C4 = (const uint4*)sC;
+#pragma unroll
+            for (int q = 0; q < WM / 4; ++q) {
+                const uint4 a = Ae4[q], cc4 = C4[q];
+                Ce[4 * q] = cc4.x & a.x;
+                Ce[4 * q + 1] = cc4.y & a.y;
+                Ce[4 * q + 2] = cc4.z & a.z;
+                Ce[4 * q + 3] = cc4.w & a.w;
+            }
+            uint32_t S = 0, nf = 0;
+#pragma unroll
+            for (int q = 0; q < WM; ++q) {
+                uint32_t bits = Ce[q];
+                while (bits) {
+                    const int f = q * 32 + __ffs(bits) - 1;
+                    bits &= bits - 1u;
+                    const uint4* F4 = (const uint4*)(A + (int64_t)f * RS);
+                    uint32_t dgr = 0;
+#pragma unroll
+                    for (int r = 0; r < WM / 4; ++r) {
+                        const uint4 a = F4[r];
+                        dgr += (uint32_t)(__popc(Ce[4 * r] & a.x) + __popc(Ce[4 * r + 1] & a.y) +
+                                          __popc(Ce[4 * r + 2] & a.z) + __popc(Ce[4 * r + 3] & a.w));
+                    }
+                    S += dgr;
+                    ++nf;
+                }
+            }
+            if (PV) {  // S = 2 T(e): twice the edges inside N(e) & C
+                const uint32_t T = S / 2u;
+                tot += T;
+                if (T) pv_add(pvlo, pvhi, e, T);
+            } else {
+                tot += S;
+            }
+            wl += (unsigned long long)(nf + 1) * (unsigned long long)Wd;
+        }
+    }
+    if (wk) *wk += warp_sum64(wl);
+    __syncwarp();
+    const unsigned long long all = warp_sum64(tot);
+    return PV ? all / 3ull : all;
 }
 
 // ------------------------------------------------ compact sub-tree (<= 64)
@@ -299,9 +458,10 @@ __device__ unsigned long long compact_count(uint32_t C, int n, int need, const u
 // Chains below a first-level choice: level 0 holds C (elements above i1),
 // need0 >= 3 vertices still to choose.  Returns the cliques completed and
 // credits chain members with their sub-tree totals (per-vertex mode).
-template <bool PV>
+template <bool PV, int WM>
 __device__ unsigned long long dfs_reg(uint32_t c0, int need0, int Wd, const uint32_t* A, int RS, uint32_t* pvlo,
-                                      uint32_t* pvhi, int lane, unsigned long long* wk, int clo, int chi)
+                                      uint32_t* pvhi, uint32_t* sC, int lane, unsigned long long* wk, int clo,
+                                      int chi)
 {
     uint32_t st[kMaxLev];
 #pragma unroll
@@ -333,9 +493,12 @@ __device__ unsigned long long dfs_reg(uint32_t c0, int need0, int Wd, const uint
         if (wk) *wk += (unsigned long long)(Wd - fw);
         const int need = need0 - t - 1;
         if (cnt < need) continue;
-        if (need == 2 || (cnt >= clo && cnt <= chi)) {
-            const unsigned long long E = need == 2 ? leaf2_reg<PV>(cn, fw, Wd, A, RS, pvlo, pvhi, lane, wk)
-                                                   : compact_count<PV>(cn, cnt, need, A, RS, pvlo, pvhi, lane, wk);
+        const bool compact = cnt >= clo && cnt <= chi;
+        if (need == 2 || compact || (WM >= 4 && need == 3)) {
+            const unsigned long long E =
+                need == 2 ? (unsigned long long)leaf2_any<PV, WM>(cn, fw, Wd, A, RS, pvlo, pvhi, lane, wk)
+                : compact ? compact_count<PV>(cn, cnt, need, A, RS, pvlo, pvhi, lane, wk)
+                          : penult3<PV, (WM >= 4 ? WM : 4)>(cn, Wd, A, RS, pvlo, pvhi, sC, lane, wk);
             total += E;
             cur_sub += E;
             if (PV && lane == 0 && E) pv_add(pvlo, pvhi, e, E);
@@ -352,18 +515,19 @@ __device__ unsigned long long dfs_reg(uint32_t c0, int need0, int Wd, const uint
     return total;
 }
 
-template <bool PV, bool COL>
+template <bool PV, bool COL, int WM>
 __global__ void __launch_bounds__(256, 4) k_dfs_reg(Ctx cb, int W, int R, int clo, int chi)
 {
     extern __shared__ __align__(16) uint32_t smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, NW = blockDim.x >> 5;
-    const int RS = W + 1;
-    const RLayout lay = make_rlayout(W, RS, PV, COL);
+    const int RS = row_stride(W, WM);
+    const RLayout lay = make_rlayout(W, RS, PV, COL, NW);
     int32_t* sL = (int32_t*)(smem + lay.L);
     uint32_t* sCol = smem + lay.col;
     uint32_t* pvlo = smem + lay.pvlo;
     uint32_t* pvhi = smem + lay.pvhi;
     uint32_t* sA = smem + lay.A;
+    __shared__ __align__(16) uint32_t s_c[8][32];  // per-warp candidate-set buffer
     __shared__ int s_next;
     __shared__ unsigned long long s_tot, s_wk;
     __shared__ long long s_item;
@@ -435,10 +599,13 @@ __global__ void __launch_bounds__(256, 4) k_dfs_reg(Ctx cb, int W, int R, int cl
                 const int cnt = (int)__reduce_add_sync(kFull, (unsigned)__popc(c0));
                 if (wkp) wk += (unsigned long long)(Wd - we);
                 if (cnt < need0) continue;
+                const bool compact = cnt >= clo && cnt <= chi;
                 const unsigned long long sub =
-                    need0 == 2 ? (unsigned long long)leaf2_reg<PV>(c0, we, Wd, sA, RS, pvlo, pvhi, lane, wkp)
-                    : (cnt >= clo && cnt <= chi) ? compact_count<PV>(c0, cnt, need0, sA, RS, pvlo, pvhi, lane, wkp)
-                                                 : dfs_reg<PV>(c0, need0, Wd, sA, RS, pvlo, pvhi, lane, wkp, clo, chi);
+                    need0 == 2 ? (unsigned long long)leaf2_any<PV, WM>(c0, we, Wd, sA, RS, pvlo, pvhi, lane, wkp)
+                    : compact  ? compact_count<PV>(c0, cnt, need0, sA, RS, pvlo, pvhi, lane, wkp)
+                    : (WM >= 4 && need0 == 3)
+                        ? penult3<PV, (WM >= 4 ? WM : 4)>(c0, Wd, sA, RS, pvlo, pvhi, s_c[wid], lane, wkp)
+                        : dfs_reg<PV, WM>(c0, need0, Wd, sA, RS, pvlo, pvhi, s_c[wid], lane, wkp, clo, chi);
                 wtot += sub;
                 if (PV && lane == 0 && sub) pv_add(pvlo, pvhi, e1, sub);
             }
@@ -482,7 +649,8 @@ kc_status dfs_reg_launch(const cc::Ctx& c, int W, bool pv, bool col, cudaStream_
     const int sms = num_sms();
     const int R = parts_per_owner(W, c.k);
     const int NW = W <= 4 ? 4 : 8;
-    const RLayout lay = make_rlayout(W, W + 1, pv, col);
+    const int WM = W <= 16 ? W : 0;  // widest class keeps the generic last level
+    const RLayout lay = make_rlayout(W, row_stride(W, WM), pv, col, NW);
     const size_t smem = (size_t)lay.total * 4;
     auto pick = [&](auto kern) -> kc_status {
         if (smem > 48 * 1024)
@@ -493,8 +661,18 @@ kc_status dfs_reg_launch(const cc::Ctx& c, int W, bool pv, bool col, cudaStream_
         KC_LAUNCHED();
         return KC_OK;
     };
-    if (pv) return col ? KC_ENOTSUP : pick(k_dfs_reg<true, false>);
-    return col ? pick(k_dfs_reg<false, true>) : pick(k_dfs_reg<false, false>);
+    auto by_width = [&](auto pv_t, auto col_t) -> kc_status {
+        constexpr bool P = decltype(pv_t)::value, Q = decltype(col_t)::value;
+        switch (WM) {
+        case 2: return pick(k_dfs_reg<P, Q, 2>);
+        case 4: return pick(k_dfs_reg<P, Q, 4>);
+        case 8: return pick(k_dfs_reg<P, Q, 8>);
+        case 16: return pick(k_dfs_reg<P, Q, 16>);
+        default: return pick(k_dfs_reg<P, Q, 0>);
+        }
+    };
+    if (pv) return col ? KC_ENOTSUP : by_width(std::true_type{}, std::false_type{});
+    return col ? by_width(std::false_type{}, std::true_type{}) : by_width(std::false_type{}, std::false_type{});
 }
 
 }  // namespace kc
