@@ -175,6 +175,31 @@ kc_status kc_estimate(const kc_graph* g, int k, uint32_t colours, uint64_t seed,
                       uint64_t* per_owner, void* stream);
 
 /*
+ * kc_estimate_pairs -- plain pair sampling (Sec. 6, "Plain pair sampling",
+ * analysed in App. B): Map 2 of owner u emits each pair x_i < x_j of
+ * Gamma+(u) with probability p, independently of every other pair and of
+ * every other owner; Reduce 3 counts the (k-1)-cliques of the sampled G+(u).
+ * A clique is sampled when all C(k-1, 2) pairs among its non-owner members
+ * were emitted, so S / p^((k-1)(k-2)/2) is an unbiased estimate of q_k.
+ *   p          in (0, 1]; pair {x, y} of Gamma+(u) is kept iff h < thr with
+ *              thr = floor(p * 2^64) (exact for p >= 2^-11) and
+ *              h = mix(mix(seed XOR (G * ((uint64)u << 32 | a))) XOR (G * b)),
+ *              G = 0x9E3779B97F4A7C15, mix the splitmix64 output function
+ *              (as for kc_estimate), a < b the caller's ids of x and y, u the
+ *              caller's id of the owner.  p = 1 keeps every pair (S = q_k).
+ *   sampled    out: S = sum of the sampled per-owner counts (exact); with
+ *              KC_DEVICE_PTRS a device array of two uint64 words (low, high)
+ *   estimate   out, host pointer, nullable: fl(S) / P where P is
+ *              p^((k-1)(k-2)/2) formed by repeated multiplication in double,
+ *              starting from 1.0; ignored with KC_DEVICE_PTRS
+ *   per_owner  out array of n, nullable: sampled q_u of every owner
+ * Errors: KC_EINVAL also for p outside (0, 1] or NaN; otherwise as kc_count.
+ */
+kc_status kc_estimate_pairs(const kc_graph* g, int k, double p, uint64_t seed,
+                            unsigned flags, uint64_t* sampled, double* estimate,
+                            uint64_t* per_owner, void* stream);
+
+/*
  * kc_footprint -- device memory a kc_count / kc_estimate call on g for k
  * allocates (stream-ordered) while it runs, for admission control.
  *   per_vertex, per_owner  nonzero if those outputs are requested

@@ -1,4 +1,5 @@
-"""CPU oracle for k-clique counting (FFF_k) and colour sampling (cFFF_k).
+"""CPU oracle for k-clique counting (FFF_k), colour sampling (cFFF_k) and
+plain pair sampling (Sec. 6).
 
 TEST INFRASTRUCTURE: only tests/, the smoke check and the benchmark's
 CPU-baseline leg import this package.  It shares no code with the CUDA
@@ -53,6 +54,17 @@ def _load():
     lib.oracle_owner_coloured.restype = ctypes.c_int
     lib.oracle_scale_estimate.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int]
     lib.oracle_scale_estimate.restype = ctypes.c_double
+    lib.oracle_pair_hash.argtypes = [ctypes.c_uint64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
+    lib.oracle_pair_hash.restype = ctypes.c_uint64
+    lib.oracle_pair_threshold.argtypes = [ctypes.c_double]
+    lib.oracle_pair_threshold.restype = ctypes.c_uint64
+    lib.oracle_scale_pairs.argtypes = [ctypes.c_uint64, ctypes.c_double, ctypes.c_int]
+    lib.oracle_scale_pairs.restype = ctypes.c_double
+    lib.oracle_fff_pairs.argtypes = [P, P, ctypes.c_int32, ctypes.c_int, ctypes.c_double, ctypes.c_uint64,
+                                     ctypes.c_int32, ctypes.c_int32, ctypes.c_int, U64P, U64P, P]
+    lib.oracle_fff_pairs.restype = ctypes.c_int
+    lib.oracle_owner_pairs.argtypes = [P, P, ctypes.c_int32, ctypes.c_int, P, U64P, U64P]
+    lib.oracle_owner_pairs.restype = ctypes.c_int
     lib.oracle_brute_force.argtypes = [P, P, ctypes.c_int32, ctypes.c_int, U64P, U64P, P]
     lib.oracle_brute_force.restype = ctypes.c_int
     lib.oracle_max_threads.argtypes = [ctypes.c_int]
@@ -160,6 +172,41 @@ def owner_coloured(g, u: int, k: int, colours_of_gamma_plus) -> int:
     lo, hi = ctypes.c_uint64(0), ctypes.c_uint64(0)
     _check(_load().oracle_owner_coloured(off.ctypes.data, adj.ctypes.data, u, k,
                                          col.ctypes.data, ctypes.byref(lo), ctypes.byref(hi)))
+    return (int(hi.value) << 64) | int(lo.value)
+
+
+def pair_hash(seed: int, u: int, x: int, y: int) -> int:
+    return int(_load().oracle_pair_hash(seed, u, x, y))
+
+
+def pair_threshold(p: float) -> int:
+    return int(_load().oracle_pair_threshold(p))
+
+
+def estimate_pairs(g, k: int, p: float, seed: int, per_owner: bool = False, u_range=None, nthreads: int = 0):
+    """Plain pair sampling (Sec. 6): returns (sampled count S,
+    estimate S / p^((k-1)(k-2)/2), per_owner S_u or None)."""
+    off, adj = _csr(g)
+    lo, hi = (0, g.n) if u_range is None else u_range
+    po = np.zeros(max(g.n, 1), dtype=np.uint64) if per_owner else None
+    tlo, thi = ctypes.c_uint64(0), ctypes.c_uint64(0)
+    _check(_load().oracle_fff_pairs(off.ctypes.data, adj.ctypes.data, g.n, k, float(p), seed, lo, hi, nthreads,
+                                    ctypes.byref(tlo), ctypes.byref(thi),
+                                    po.ctypes.data if po is not None else None))
+    s = (int(thi.value) << 64) | int(tlo.value)
+    return s, float(_load().oracle_scale_pairs(s, float(p), k)), (po[: g.n] if po is not None else None)
+
+
+def owner_pairs(g, u: int, k: int, kept) -> int:
+    """Reduce 3's count for owner u when Map 2 emitted exactly the pairs (i, j),
+    i < j, with kept[i, j] set (indices of Gamma+(u) in precedence order)."""
+    off, adj = _csr(g)
+    kept = np.ascontiguousarray(kept, dtype=np.uint8)
+    if kept.size == 0:
+        kept = np.zeros(1, dtype=np.uint8)
+    lo, hi = ctypes.c_uint64(0), ctypes.c_uint64(0)
+    _check(_load().oracle_owner_pairs(off.ctypes.data, adj.ctypes.data, u, k, kept.ctypes.data,
+                                      ctypes.byref(lo), ctypes.byref(hi)))
     return (int(hi.value) << 64) | int(lo.value)
 
 

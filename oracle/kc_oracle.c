@@ -133,6 +133,35 @@ uint32_t oracle_colour(uint64_t seed, int32_t u, int32_t x, uint32_t c)
     return (uint32_t)(((u128)oracle_colour_hash(seed, u, x) * (u128)c) >> 64);
 }
 
+/* ---------------------------------- plain pair sampling (Sec. 6) */
+
+/* Map 2 of owner u emits the pair {x, y} of Gamma+(u) with probability p,
+ * independently per pair and per owner (Sec. 6, App. B).  Counter-based: with
+ * a < b the two ids, h = mix(mix(seed XOR G * (u<<32 | a)) XOR G * b), and the
+ * pair is emitted iff h < thr, thr = floor(p * 2^64) (p < 1). */
+uint64_t oracle_pair_hash(uint64_t seed, int32_t u, int32_t x, int32_t y)
+{
+    uint32_t a = (uint32_t)x < (uint32_t)y ? (uint32_t)x : (uint32_t)y;
+    uint32_t b = (uint32_t)x < (uint32_t)y ? (uint32_t)y : (uint32_t)x;
+    uint64_t z = mix64(seed ^ (0x9E3779B97F4A7C15ULL * (((uint64_t)(uint32_t)u << 32) | a)));
+    return mix64(z ^ (0x9E3779B97F4A7C15ULL * (uint64_t)b));
+}
+
+/* floor(p * 2^64) for 0 < p < 1 (the product by a power of two is exact). */
+uint64_t oracle_pair_threshold(double p)
+{
+    return (uint64_t)(p * 18446744073709551616.0);
+}
+
+/* Estimate of plain pair sampling: fl(S) / p^((k-1)(k-2)/2), the power formed
+ * by repeated multiplication in double starting from 1.0 (Sec. 6). */
+double oracle_scale_pairs(uint64_t sampled, double p, int k)
+{
+    double f = 1.0;
+    for (int i = 0; i < (k - 1) * (k - 2) / 2; ++i) f *= p;
+    return (double)sampled / f;
+}
+
 /* -------------------------------------- Reduce 3: cliques in G+(u) */
 
 typedef struct {
@@ -192,16 +221,28 @@ static u128 count_rec(rec_ctx* c, const int32_t* cand, int32_t ncand, int s)
     return total;
 }
 
-/* FFF_k (colours == 0) or cFFF_k (colours >= 1) work for one owner u: Round 1
- * gives Gamma+(u); Reduce 1 drops u when |Gamma+(u)| < k-1; Map 2 emits the
- * pairs x_i precedes x_j of Gamma+(u) (only monochromatic pairs under cFFF_k,
- * Sec. 6); Reduce 2 keeps a pair when it is an edge of G (the "$" marker);
- * Reduce 3 counts the (k-1)-cliques of the resulting G+(u).  The explicit
- * colour array (indexed like Gamma+(u)) overrides the hash when given. */
+/* FFF_k, cFFF_k or plain pair sampling work for one owner u: Round 1 gives
+ * Gamma+(u); Reduce 1 drops u when |Gamma+(u)| < k-1; Map 2 emits the pairs
+ * x_i precedes x_j of Gamma+(u) (only monochromatic pairs under cFFF_k, only
+ * the pairs whose coin came up under pair sampling, Sec. 6); Reduce 2 keeps a
+ * pair when it is an edge of G (the "$" marker); Reduce 3 counts the
+ * (k-1)-cliques of the resulting G+(u).  An explicit colour array or kept-pair
+ * matrix (indexed like Gamma+(u)) overrides the hash when given. */
+typedef struct {
+    uint32_t colours;             /* cFFF_k: >= 1 colours (0: no colouring) */
+    uint64_t seed;
+    const uint32_t* given_colour; /* explicit colouring of Gamma+(u), or NULL */
+    int pair;                     /* plain pair sampling with threshold pthr */
+    uint64_t pthr;
+    const uint8_t* given_kept;    /* explicit emitted pairs (d+ x d+, row i, column j > i), or NULL */
+} sampler;
+
 static int owner_work(const int64_t* off, const int32_t* adj, int32_t u, int k,
-                      uint32_t colours, uint64_t seed, const uint32_t* given_colour,
-                      uint64_t* per_vertex, u128* q_u)
+                      const sampler* sm, uint64_t* per_vertex, u128* q_u)
 {
+    uint32_t colours = sm->colours;
+    uint64_t seed = sm->seed;
+    const uint32_t* given_colour = sm->given_colour;
     *q_u = 0;
     int64_t d = degree(off, u);
     int32_t* L = (int32_t*)malloc((size_t)(d > 0 ? d : 1) * sizeof(int32_t));
@@ -230,6 +271,9 @@ static int owner_work(const int64_t* off, const int32_t* adj, int32_t u, int k,
             if (!out[i]) { st = OR_ENOMEM; goto done; }
             for (int32_t j = i + 1; j < dp; ++j) {
                 if (col && col[i] != col[j]) continue;          /* Map 2 sampling */
+                if (sm->given_kept && !sm->given_kept[(int64_t)i * dp + j]) continue;
+                if (!sm->given_kept && sm->pair &&
+                    oracle_pair_hash(sm->seed, u, L[i], L[j]) >= sm->pthr) continue;
                 if (adjacent(off, adj, L[i], L[j]))            /* Reduce 2 "$" */
                     out[i][outlen[i]++] = j;
             }
@@ -255,10 +299,10 @@ done:
  *   nthreads: OpenMP threads over owners (<= 0: library default).
  * k = 1 counts vertices (q_1 = n) and k = 2 edges (q_2 = m), as in the
  * paper's tables. */
-int oracle_fff(const int64_t* off, const int32_t* adj, int32_t n, int k,
-               uint32_t colours, uint64_t seed, int32_t u_lo, int32_t u_hi,
-               int nthreads, uint64_t* total_lo, uint64_t* total_hi,
-               uint64_t* per_owner, uint64_t* per_vertex)
+static int fff_run(const int64_t* off, const int32_t* adj, int32_t n, int k,
+                   const sampler* sm, int32_t u_lo, int32_t u_hi,
+                   int nthreads, uint64_t* total_lo, uint64_t* total_hi,
+                   uint64_t* per_owner, uint64_t* per_vertex)
 {
     if (n < 0 || k < 1 || u_lo < 0 || u_hi > n || u_lo > u_hi) return OR_EINVAL;
     u128 total = 0;
@@ -290,7 +334,7 @@ int oracle_fff(const int64_t* off, const int32_t* adj, int32_t n, int k,
             tid = omp_get_thread_num();
 #endif
             u128 q = 0;
-            int s = owner_work(off, adj, u, k, colours, seed, NULL, per_vertex, &q);
+            int s = owner_work(off, adj, u, k, sm, per_vertex, &q);
             if (s != OR_OK) {
 #ifdef _OPENMP
 #pragma omp critical
@@ -317,13 +361,50 @@ int oracle_fff(const int64_t* off, const int32_t* adj, int32_t n, int k,
     return st;
 }
 
+int oracle_fff(const int64_t* off, const int32_t* adj, int32_t n, int k,
+               uint32_t colours, uint64_t seed, int32_t u_lo, int32_t u_hi,
+               int nthreads, uint64_t* total_lo, uint64_t* total_hi,
+               uint64_t* per_owner, uint64_t* per_vertex)
+{
+    sampler sm = { colours, seed, NULL, 0, 0, NULL };
+    return fff_run(off, adj, n, k, &sm, u_lo, u_hi, nthreads, total_lo, total_hi, per_owner, per_vertex);
+}
+
+/* Plain pair sampling (Sec. 6) over owners u in [u_lo, u_hi): the sampled
+ * count S (before scaling) and per-owner sampled counts; p in (0, 1], p = 1
+ * emits every pair. */
+int oracle_fff_pairs(const int64_t* off, const int32_t* adj, int32_t n, int k,
+                     double p, uint64_t seed, int32_t u_lo, int32_t u_hi,
+                     int nthreads, uint64_t* total_lo, uint64_t* total_hi,
+                     uint64_t* per_owner)
+{
+    if (!(p > 0.0 && p <= 1.0)) return OR_EINVAL;
+    sampler sm = { 0, seed, NULL, p < 1.0, p < 1.0 ? oracle_pair_threshold(p) : 0, NULL };
+    return fff_run(off, adj, n, k, &sm, u_lo, u_hi, nthreads, total_lo, total_hi, per_owner, NULL);
+}
+
 /* Reduce 3 output for one owner u under an explicit colouring of Gamma+(u)
  * (colour[i] is the colour of the i-th element in precedence order). */
 int oracle_owner_coloured(const int64_t* off, const int32_t* adj, int32_t u, int k,
                           const uint32_t* colour, uint64_t* q_lo, uint64_t* q_hi)
 {
     u128 q = 0;
-    int st = owner_work(off, adj, u, k, 0, 0, colour, NULL, &q);
+    sampler sm = { 0, 0, colour, 0, 0, NULL };
+    int st = owner_work(off, adj, u, k, &sm, NULL, &q);
+    *q_lo = (uint64_t)q;
+    *q_hi = (uint64_t)(q >> 64);
+    return st;
+}
+
+/* Reduce 3 output for one owner u when Map 2 emitted exactly the pairs with
+ * kept[i * d + j] != 0 (i < j indices of Gamma+(u) in precedence order,
+ * d = |Gamma+(u)|). */
+int oracle_owner_pairs(const int64_t* off, const int32_t* adj, int32_t u, int k,
+                       const uint8_t* kept, uint64_t* q_lo, uint64_t* q_hi)
+{
+    u128 q = 0;
+    sampler sm = { 0, 0, NULL, 1, 0, kept };
+    int st = owner_work(off, adj, u, k, &sm, NULL, &q);
     *q_lo = (uint64_t)q;
     *q_hi = (uint64_t)(q >> 64);
     return st;

@@ -1,4 +1,5 @@
 // api.cu -- the extern "C" entry points of libkc (declared in include/kc.h).
+#include <cmath>
 #include <algorithm>
 #include <atomic>
 #include <cstdio>
@@ -105,7 +106,7 @@ kc_status copy_out_u64(uint64_t* dst, const unsigned long long* src, int32_t n, 
 // Shared body of kc_count and kc_estimate.
 kc_status run_count(const kc_graph* g, int k, uint32_t colours, uint64_t seed, unsigned flags,
                     uint64_t* total, uint64_t* per_vertex, uint64_t* per_owner, cudaStream_t s, int part = 0,
-                    int nparts = 1)
+                    int nparts = 1, bool pair = false, uint64_t pthr = 0)
 {
     const bool dev = (flags & KC_DEVICE_PTRS) != 0;
     const int32_t n = g->n;
@@ -162,6 +163,8 @@ kc_status run_count(const kc_graph* g, int k, uint32_t colours, uint64_t seed, u
         a.k = k;
         a.colours = colours;
         a.seed = seed;
+        a.pair = pair;
+        a.pthr = pthr;
         a.per_vertex = per_vertex != nullptr;
         a.total = small;
         a.pv = pv_rank;
@@ -325,6 +328,25 @@ kc_status kc_estimate(const kc_graph* g, int k, uint32_t colours, uint64_t seed,
         double f = 1.0;
         for (int i = 0; i < k - 2; ++i) f *= (double)colours;
         *estimate = (double)*sampled * f;
+    }
+    return KC_OK;
+}
+
+kc_status kc_estimate_pairs(const kc_graph* g, int k, double p, uint64_t seed, unsigned flags, uint64_t* sampled,
+                            double* estimate, uint64_t* per_owner, void* stream)
+{
+    if (!g || !sampled || k < 1 || k > KC_MAX_K || !(p > 0.0 && p <= 1.0)) return KC_EINVAL;
+    kc::DeviceGuard dg(g->device);
+    // p = 1 keeps every pair: the exact count
+    const bool pair = p < 1.0;
+    const uint64_t thr = pair ? (uint64_t)std::ldexp(p, 64) : 0;
+    kc_status st = kc::run_count(g, k, 0, seed, flags, sampled, nullptr, per_owner, (cudaStream_t)stream, 0, 1,
+                                 pair, thr);
+    if (st != KC_OK) return st;
+    if (estimate && !(flags & KC_DEVICE_PTRS)) {
+        double f = 1.0;
+        for (int i = 0; i < (k - 1) * (k - 2) / 2; ++i) f *= p;
+        *estimate = (double)*sampled / f;
     }
     return KC_OK;
 }

@@ -64,7 +64,6 @@ namespace {
 
 using cc::Ctx;
 using cc::add_total;
-using cc::colour_of;
 using cc::mask_above;
 using cc::mask_below;
 using cc::warp_sum64;
@@ -99,10 +98,11 @@ __global__ void __launch_bounds__(256) k_count_w1(Ctx cb)
         const int d = (int)(c.offp[r + 1] - b);
         const int32_t x = lane < d ? c.adjp[b + lane] : INT_MAX;
         uint32_t col = 0;
-        if (COL && lane < d) col = colour_of(c.seed, c.perm[r], c.perm[x], c.colours);
+        const int32_t ur = COL ? c.perm[r] : 0;
+        if (COL && lane < d) col = cc::sample_label(c, ur, c.perm[x]);
 
         // (b) rows: lane j searches x_j in each 32-entry chunk of Gamma+(x_i)
-        const uint32_t up = cc::build_rows_w1<COL>(c, x, d, col, lane);
+        const uint32_t up = cc::build_rows_w1<COL>(c, x, d, col, ur, lane);
         const uint32_t A = PV ? (up | cc::lower_rows_w1(up, d, lane)) : up;
 
         // (c) depth-first search; level t's state of the chain is kept in lane t
@@ -345,7 +345,7 @@ __global__ void __launch_bounds__(256) k_count_cta(Ctx cb, int W, int levels, ui
         for (int j = threadIdx.x; j < d; j += blockDim.x) {
             const int32_t x = c.adjp[b + j];
             sL[j] = x;
-            if (COL) sCol[j] = colour_of(c.seed, ur, c.perm[x], c.colours);
+            if (COL) sCol[j] = cc::sample_label(c, ur, c.perm[x]);
             if (PV) sPV[j] = 0ull;
         }
         for (int64_t j = threadIdx.x; j < (int64_t)d * RS; j += blockDim.x) sA[j] = 0u;
@@ -357,7 +357,7 @@ __global__ void __launch_bounds__(256) k_count_cta(Ctx cb, int W, int levels, ui
         const int Wd = (d + 31) >> 5;  // words in use by this owner
 
         // (b) + (d): rows, split over warps
-        cc::build_rows<PV, COL>(c, sL, sCol, d, sA, RS, wid, NW, lane);
+        cc::build_rows<PV, COL>(c, sL, sCol, d, sA, RS, wid, NW, lane, ur);
         __syncthreads();
 
         // (c) count
@@ -504,6 +504,8 @@ Ctx base_ctx(const CountArgs& a)
     c.k = a.k;
     c.colours = a.colours;
     c.seed = a.seed;
+    c.pair = a.pair ? 1 : 0;
+    c.pthr = a.pthr;
     c.total = a.total;
     c.pv = a.pv;
     c.po = a.po;
@@ -576,7 +578,7 @@ kc_status count_launch(const kc_graph* g, const CountArgs& a, unsigned long long
     base.queue = g->queue;
     base.perm = g->perm;
     const int64_t part = a.nparts > 1 ? a.part : 0, nparts = a.nparts > 1 ? a.nparts : 1;
-    const bool col = a.colours >= 2;  // one colour keeps every pair
+    const bool col = a.colours >= 2 || a.pair;  // one colour keeps every pair
     const int Wh = (g->max_dplus + 31) / 32;
     for (int slot = 0; slot < kOwnerSlots; ++slot) {
         Ctx c = base;
@@ -598,7 +600,7 @@ kc_status count_batch_launch(const kc_graph* const* gs, int ng, const CountArgs&
     Ctx base = base_ctx(a);
     base.gd = (const cc::GraphDesc*)descs;
     base.ng = ng;
-    const bool col = a.colours >= 2;
+    const bool col = a.colours >= 2 || a.pair;
     int Wh = 1;
     for (int g = 0; g < ng; ++g) Wh = std::max(Wh, (gs[g]->max_dplus + 31) / 32);
     // per slot: gq0[ng] then gpre[ng + 1]

@@ -39,6 +39,8 @@ struct Ctx {
     int k;
     uint32_t colours;
     uint64_t seed;
+    int pair;        // plain pair sampling instead of colours (Sec. 6)
+    uint64_t pthr;   // pair kept iff its hash < pthr
     unsigned long long* total;
     unsigned long long* pv;
     unsigned long long* po;
@@ -83,6 +85,36 @@ __device__ __forceinline__ uint32_t colour_of(uint64_t seed, int32_t u, int32_t 
     return (uint32_t)__umul64hi(z, (uint64_t)c);
 }
 
+// Pair sampling (Sec. 6, plain pair sampling): the pair {x, y} of Gamma+(u)
+// is kept iff h < thr, h = F(F(seed ^ G (u<<32 | a)) ^ G b) with a < b the
+// two original ids and F the splitmix64 output function (spec in kc.h).
+__device__ __forceinline__ bool pair_kept(uint64_t seed, int32_t u, uint32_t x, uint32_t y, uint64_t thr)
+{
+    const uint32_t a = x < y ? x : y, b = x < y ? y : x;
+    uint64_t z = seed ^ (0x9E3779B97F4A7C15ull * (((uint64_t)(uint32_t)u << 32) | (uint64_t)a));
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    z ^= 0x9E3779B97F4A7C15ull * (uint64_t)b;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return z < thr;
+}
+
+// The per-node label a sampling filter keeps for x_j of Gamma+(u) (ur, xid:
+// original ids): its colour under cFFF_k, its id under pair sampling.
+__device__ __forceinline__ uint32_t sample_label(const Ctx& c, int32_t ur, int32_t xid)
+{
+    return c.pair ? (uint32_t)xid : colour_of(c.seed, ur, xid, c.colours);
+}
+
+// Whether the pair with labels li, lj survives the sampling filter.
+__device__ __forceinline__ bool sample_keep(const Ctx& c, int32_t ur, uint32_t li, uint32_t lj)
+{
+    return c.pair ? pair_kept(c.seed, ur, li, lj, c.pthr) : li == lj;
+}
+
 // 128-bit total as (lo, hi) words.
 __device__ __forceinline__ void add_total(unsigned long long* t, unsigned long long v)
 {
@@ -106,9 +138,11 @@ __device__ __forceinline__ uint32_t mask_below(int b) { return (1u << b) - 1u; }
 // lane j holds x_j (rank, INT_MAX past d); returns, in lane i, the word whose
 // bit j (j > i) is set iff x_j is in Gamma+(x_i) -- each Gamma+(x_i) chunk of
 // 32 entries is searched for x_j by a shuffle binary search, and the scan
-// stops at max Gamma+(u).  cFFF_k keeps only pairs of equal colour.
+// stops at max Gamma+(u).  Under sampling (COL) lane j holds x_j's label and
+// only pairs passing sample_keep are kept (ur: u's original id).
 template <bool COL>
-__device__ __forceinline__ uint32_t build_rows_w1(const Ctx& c, int32_t x, int d, uint32_t col, int lane)
+__device__ __forceinline__ uint32_t build_rows_w1(const Ctx& c, int32_t x, int d, uint32_t col, int32_t ur,
+                                                  int lane)
 {
     const int32_t maxL = __shfl_sync(kFull, x, d - 1);
     uint32_t up = 0;
@@ -129,7 +163,7 @@ __device__ __forceinline__ uint32_t build_rows_w1(const Ctx& c, int32_t x, int d
             row |= __ballot_sync(kFull, lane > i && lane < d && yl == x);
             if (__shfl_sync(kFull, y, 31) >= maxL) break;
         }
-        if (COL) row &= __ballot_sync(kFull, col == __shfl_sync(kFull, col, i));
+        if (COL) row &= __ballot_sync(kFull, sample_keep(c, ur, __shfl_sync(kFull, col, i), col));
         if (lane == i) up = row;
     }
     return up;
@@ -149,10 +183,11 @@ __device__ __forceinline__ uint32_t lower_rows_w1(uint32_t up, int d, int lane)
 
 // Rows of G+(u) into a bitmap A (row stride RS words, zeroed beforehand) by
 // warps w0, w0+nw, ... of the caller; sL holds Gamma+(u) (ranks, ascending),
-// sCol their colours under cFFF_k.  With SYM the bitmap is made symmetric.
+// sCol their sampling labels (COL; ur: u's original id).  With SYM the
+// bitmap is made symmetric.
 template <bool SYM, bool COL>
 __device__ __forceinline__ void build_rows(const Ctx& c, const int32_t* sL, const uint32_t* sCol, int d,
-                                           uint32_t* A, int RS, int w0, int nw, int lane)
+                                           uint32_t* A, int RS, int w0, int nw, int lane, int32_t ur = 0)
 {
     const int32_t maxL = sL[d - 1];
     for (int i = w0; i < d - 1; i += nw) {
@@ -168,7 +203,7 @@ __device__ __forceinline__ void build_rows(const Ctx& c, const int32_t* sL, cons
                     const int mid = (lo + hi) >> 1;
                     if (sL[mid] < y) lo = mid + 1; else hi = mid;
                 }
-                if (lo < d && sL[lo] == y && (!COL || sCol[lo] == ci)) {
+                if (lo < d && sL[lo] == y && (!COL || sample_keep(c, ur, ci, sCol[lo]))) {
                     atomicOr(&A[(int64_t)i * RS + (lo >> 5)], 1u << (lo & 31));
                     if (SYM) atomicOr(&A[(int64_t)lo * RS + (i >> 5)], 1u << (i & 31));
                 }

@@ -35,7 +35,6 @@ int num_sms();
 namespace {
 
 using cc::add_total;
-using cc::colour_of;
 using cc::Ctx;
 using cc::mask_above;
 using cc::mask_below;
@@ -302,7 +301,18 @@ __device__ unsigned long long penult3(uint32_t C, int Wd, const uint32_t* A, int
             } else {
                 tot += S;
             }
-            wl += (unsigned long long)(nf + 1) * (unsigned long long)Wd;
+            if (wk) {
+                // work of the ordered search this replaces: forming the child's
+                // set and one row operation per member above e
+                uint32_t up = nf;
+                if (PV) {
+                    up = 0;
+#pragma unroll
+                    for (int q = 0; q < WM; ++q)
+                        up += (uint32_t)__popc(q < (e >> 5) ? 0u : (q == (e >> 5) ? Ce[q] & cc::mask_above(e & 31) : Ce[q]));
+                }
+                wl += (unsigned long long)(up + 1) * (unsigned long long)Wd;
+            }
         }
     }
     if (wk) *wk += warp_sum64(wl);
@@ -547,7 +557,7 @@ __global__ void __launch_bounds__(256, 4) k_dfs_reg(Ctx cb, int W, int R, int cl
         for (int j = threadIdx.x; j < d; j += blockDim.x) {
             const int32_t x = c.adjp[b + j];
             sL[j] = x;
-            if (COL) sCol[j] = colour_of(c.seed, ur, c.perm[x], c.colours);
+            if (COL) sCol[j] = cc::sample_label(c, ur, c.perm[x]);
             if (PV) {
                 pvlo[j] = 0u;
                 pvhi[j] = 0u;
@@ -560,7 +570,7 @@ __global__ void __launch_bounds__(256, 4) k_dfs_reg(Ctx cb, int W, int R, int cl
             s_wk = 0ull;
         }
         __syncthreads();
-        cc::build_rows<PV, COL>(c, sL, sCol, d, sA, RS, wid, NW, lane);
+        cc::build_rows<PV, COL>(c, sL, sCol, d, sA, RS, wid, NW, lane, ur);
         __syncthreads();
 
         unsigned long long wtot = 0, wk = 0;

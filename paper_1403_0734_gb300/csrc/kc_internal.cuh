@@ -101,6 +101,8 @@ struct CountArgs {
     int k;
     uint32_t colours;       // 0: exact FFF_k; >= 1: cFFF_k
     uint64_t seed;
+    bool pair = false;      // plain pair sampling (Sec. 6): keep a pair iff its hash < pthr
+    uint64_t pthr = 0;
     bool per_vertex;        // accumulate memberships into pv (rank space)
     unsigned long long* total;  // [2] 128-bit total (lo, hi)
     unsigned long long* pv;     // [n] rank space, nullable

@@ -37,7 +37,6 @@ int slot_words(int slot);
 namespace {
 
 using cc::add_total;
-using cc::colour_of;
 using cc::Ctx;
 
 // C(n, r) for 0 <= r, exact; sets *ovf when the value does not fit 64 bits.
@@ -74,8 +73,9 @@ __global__ void __launch_bounds__(256) k_sct_w1(Ctx cb)
         const int d = (int)(c.offp[r + 1] - b);
         const int32_t x = lane < d ? c.adjp[b + lane] : INT_MAX;
         uint32_t col = 0;
-        if (COL && lane < d) col = colour_of(c.seed, c.perm[r], c.perm[x], c.colours);
-        const uint32_t up = cc::build_rows_w1<COL>(c, x, d, col, lane);
+        const int32_t ur = COL ? c.perm[r] : 0;
+        if (COL && lane < d) col = cc::sample_label(c, ur, c.perm[x]);
+        const uint32_t up = cc::build_rows_w1<COL>(c, x, d, col, ur, lane);
         const uint32_t A = up | cc::lower_rows_w1(up, d, lane);  // N(lane) inside G+(u)
 
         const bool cw = c.work != nullptr;
@@ -252,13 +252,13 @@ __global__ void __launch_bounds__(256) k_sct_warp(Ctx cb, int W, uint32_t* gscra
         for (int j = lane; j < d; j += 32) {
             const int32_t xj = c.adjp[b + j];
             sL[j] = xj;
-            if (COL) sCol[j] = colour_of(c.seed, ur, c.perm[xj], c.colours);
+            if (COL) sCol[j] = cc::sample_label(c, ur, c.perm[xj]);
             if (PV) sPV[j] = 0ull;
         }
         for (int64_t j = lane; j < (int64_t)d * RS; j += 32) sA[j] = 0u;
         for (int w = lane; w < Wd; w += 32) cur[w] = w < (d >> 5) ? kFull : ((1u << (d & 31)) - 1u);
         __syncwarp();
-        cc::build_rows<true, COL>(c, sL, sCol, d, sA, RS, 0, 1, lane);
+        cc::build_rows<true, COL>(c, sL, sCol, d, sA, RS, 0, 1, lane, ur);
         __syncwarp();
 
         const bool cw = c.work != nullptr;

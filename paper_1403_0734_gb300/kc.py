@@ -77,6 +77,9 @@ def _load():
     lib.kc_count.restype = st
     lib.kc_estimate.argtypes = [_P, ctypes.c_int, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint, _P, _P, _P, _P]
     lib.kc_estimate.restype = st
+    lib.kc_estimate_pairs.argtypes = [_P, ctypes.c_int, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint, _P, _P, _P,
+                                      _P]
+    lib.kc_estimate_pairs.restype = st
     lib.kc_count_csr.argtypes = [_P, _P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int, ctypes.c_uint, _P, _P, _P, _P]
     lib.kc_count_csr.restype = st
     lib.kc_estimate_csr.argtypes = [_P, _P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int, ctypes.c_uint32,
@@ -280,6 +283,18 @@ def estimate(g: Graph, k: int, colours: int, seed: int, per_owner: bool = False,
     est = ctypes.c_double(0.0)
     _check(_load().kc_estimate(g.handle, k, colours, seed, 0, ctypes.byref(s), ctypes.byref(est), _ptr(po),
                                _stream_handle(stream)), f"kc_estimate(k={k}, c={colours})")
+    return int(s.value), float(est.value), (po[: g.n] if po is not None else None)
+
+
+def estimate_pairs(g: Graph, k: int, p: float, seed: int, per_owner: bool = False, stream=None):
+    """Plain pair sampling on the device (Sec. 6): every pair of Gamma+(u) is
+    kept with probability p.  Returns (sampled S, estimate S / p^((k-1)(k-2)/2),
+    per_owner or None)."""
+    po = np.empty(max(g.n, 1), np.uint64) if per_owner else None
+    s = ctypes.c_uint64(0)
+    est = ctypes.c_double(0.0)
+    _check(_load().kc_estimate_pairs(g.handle, k, float(p), seed, 0, ctypes.byref(s), ctypes.byref(est), _ptr(po),
+                                     _stream_handle(stream)), f"kc_estimate_pairs(k={k}, p={p})")
     return int(s.value), float(est.value), (po[: g.n] if po is not None else None)
 
 

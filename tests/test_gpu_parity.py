@@ -210,6 +210,40 @@ def test_estimate_global_tiles(kc):
         kc.set_param(kc.KC_PARAM_SMEM_MAX_WORDS, 32)
 
 
+@pytest.mark.parametrize("name", ["chunglu_20k", "sbm_20k", "rmat_s12"])
+def test_estimate_pairs_matches_oracle(kc, name):
+    """Plain pair sampling (Sec. 6): sampled count and per-owner counts
+    bit-exact, estimate identical."""
+    g = graph(name)
+    G = kc.orient(g.off, g.adj)
+    for k in (3, 4, 5, 6):
+        for p, seed in ((0.5, 1), (0.3, 7), (0.9, 2), (0.1, 3)):
+            s, est, po = kc.estimate_pairs(G, k, p, seed, per_owner=True)
+            os_, oest, opo = oracle.estimate_pairs(g, k, p, seed, per_owner=True)
+            assert s == os_, (name, k, p, seed, s, os_)
+            assert est == oest
+            assert np.array_equal(po, opo)
+
+
+def test_estimate_pairs_edges_and_tiles(kc):
+    g = graph("chunglu_20k")
+    G = kc.orient(g.off, g.adj)
+    for k in (3, 5):  # p = 1 keeps every pair
+        s, est, _ = kc.estimate_pairs(G, k, 1.0, 99)
+        assert s == kc.count(G, k)[0] and est == float(s)
+    for bad in (0.0, -0.5, 1.5, float("nan")):
+        with pytest.raises(kc.KcError):
+            kc.estimate_pairs(G, 3, bad, 1)
+    kc.set_param(kc.KC_PARAM_SMEM_MAX_WORDS, 1)
+    try:
+        g = graph("rmat_s14")
+        G = kc.orient(g.off, g.adj)
+        for k, p in ((3, 0.5), (4, 0.7), (5, 0.8)):
+            assert kc.estimate_pairs(G, k, p, 5)[0] == oracle.estimate_pairs(g, k, p, 5)[0]
+    finally:
+        kc.set_param(kc.KC_PARAM_SMEM_MAX_WORDS, 32)
+
+
 # ------------------------------------------------------------ edge cases
 
 def test_edge_cases(kc):

@@ -286,3 +286,124 @@ def test_estimator_mean_over_seeds():
     exact = oracle.count(g, k)[0]
     ests = np.array([oracle.estimate(g, k, c, seed)[1] for seed in range(1, S + 1)])
     assert abs(ests.mean() - exact) <= 4.0 * ests.std(ddof=1) / np.sqrt(S) + 1e-9
+
+
+# ---------------------------------------------------- plain pair sampling (Sec. 6)
+
+def test_pair_threshold_is_exact_probability():
+    """thr = floor(p 2^64); for p >= 2^-11 the kept fraction thr / 2^64 is p."""
+    from fractions import Fraction
+    for p in (0.5, 0.25, 0.1, 0.3, 0.999, 2.0 ** -11):
+        thr = oracle.pair_threshold(p)
+        assert Fraction(thr, 2 ** 64) == Fraction(p)
+
+
+def test_pair_hash_symmetric_and_owner_dependent():
+    for (u, x, y) in [(0, 1, 2), (5, 100, 7), (2**31 - 1, 0, 2**31 - 2)]:
+        assert oracle.pair_hash(9, u, x, y) == oracle.pair_hash(9, u, y, x)
+    hs = {oracle.pair_hash(9, u, 3, 4) for u in range(64)}
+    assert len(hs) == 64
+    assert oracle.pair_hash(9, 0, 3, 4) != oracle.pair_hash(10, 0, 3, 4)
+
+
+def test_pair_keep_frequency():
+    """Each pair is kept with probability p: 4e4 pairs, within 5 sigma."""
+    p = 0.3
+    thr = oracle.pair_threshold(p)
+    N = 40000
+    kept = sum(oracle.pair_hash(11, u, x, x + 1 + u % 7) < thr for u in range(200) for x in range(200))
+    assert abs(kept - p * N) <= 5 * np.sqrt(N * p * (1 - p))
+
+
+def test_pairs_p1_is_exact():
+    g = kcgen.chung_lu(2000, 12000, 2.1, 200.0, 3)
+    for k in (3, 4, 5):
+        s, est, po = oracle.estimate_pairs(g, k, 1.0, 5, per_owner=True)
+        q, qo, _ = oracle.count(g, k, per_owner=True)
+        assert s == q and est == float(q) and np.array_equal(po, qo)
+
+
+@pytest.mark.parametrize("k", [3, 4, 5])
+def test_pairs_brute_force(k):
+    """S = number of (k-1)-subsets Q of Gamma+(u), over all u, whose pairs are
+    all edges and all emitted by Map 2 (hash below the threshold) -- the
+    sampled cliques of Sec. 6 -- by itertools."""
+    g = kcgen.random_small(18, 0.55, 23)
+    nbr = [set(g.adj[g.off[v]:g.off[v + 1]].tolist()) for v in range(g.n)]
+    deg = [len(s) for s in nbr]
+    p, seed = 0.6, 77
+    thr = oracle.pair_threshold(p)
+    S = 0
+    for u in range(g.n):
+        gp = [x for x in nbr[u] if (deg[u], u) < (deg[x], x)]
+        for Q in combinations(gp, k - 1):
+            if all(b in nbr[a] and oracle.pair_hash(seed, u, a, b) < thr for a, b in combinations(Q, 2)):
+                S += 1
+    s, est, _ = oracle.estimate_pairs(g, k, p, seed)
+    assert s == S
+    assert S > 0
+
+
+@pytest.mark.parametrize("k", [3, 4])
+def test_pairs_estimator_unbiased_exhaustive(k):
+    """E[q_u / p^((k-1)(k-2)/2)] = q_{u,k-1} exactly over all 2^C(d,2) sets of
+    emitted pairs of Gamma+(u) weighted by p^|K| (1-p)^(P-|K|) (Claim in
+    App. B), with p = 1/3 in exact rationals."""
+    from fractions import Fraction
+    g = kcgen.random_small(14, 0.7, 5)
+    p = Fraction(1, 3)
+    e = (k - 1) * (k - 2) // 2
+    checked = 0
+    for u in range(g.n):
+        d = len(oracle.gamma_plus(g, u))
+        if d < k - 1 or d > 5:
+            continue
+        pairs = [(i, j) for i in range(d) for j in range(i + 1, d)]
+        P = len(pairs)
+        exact = oracle.owner_pairs(g, u, k, np.ones((d, d), np.uint8))
+        acc = Fraction(0)
+        for bits in range(1 << P):
+            kept = np.zeros((d, d), np.uint8)
+            nk = 0
+            for t, (i, j) in enumerate(pairs):
+                if bits >> t & 1:
+                    kept[i, j] = 1
+                    nk += 1
+            acc += p ** nk * (1 - p) ** (P - nk) * oracle.owner_pairs(g, u, k, kept)
+        assert acc / p ** e == exact
+        checked += 1
+    assert checked >= 3
+
+
+def test_pairs_hashed_equals_explicit():
+    """The hashed Map 2 filter equals the explicit kept-pair matrix built from
+    the same hash, owner by owner."""
+    g = kcgen.random_small(30, 0.5, 8)
+    k, p, seed = 4, 0.5, 3
+    thr = oracle.pair_threshold(p)
+    _, _, po = oracle.estimate_pairs(g, k, p, seed, per_owner=True)
+    for u in range(g.n):
+        L = oracle.gamma_plus(g, u)
+        d = len(L)
+        kept = np.zeros((max(d, 1), max(d, 1)), np.uint8)
+        for i in range(d):
+            for j in range(i + 1, d):
+                kept[i, j] = oracle.pair_hash(seed, u, int(L[i]), int(L[j])) < thr
+        assert oracle.owner_pairs(g, u, k, kept) == int(po[u])
+
+
+def test_pairs_scaling():
+    """fl(S) / p^e, e = (k-1)(k-2)/2: with p = 1/2 the scale is exactly 2^e."""
+    g = kcgen.chung_lu(2000, 12000, 2.1, 200.0, 3)
+    for k in (3, 4, 5, 6):
+        e = (k - 1) * (k - 2) // 2
+        s, est, _ = oracle.estimate_pairs(g, k, 0.5, 1)
+        assert est == s * 2.0 ** e
+
+
+def test_pairs_mean_over_seeds():
+    g = kcgen.chung_lu(2000, 20000, 2.1, 250.0, 10)
+    k, p, S = 4, 0.5, 64
+    exact = oracle.count(g, k)[0]
+    ests = np.array([oracle.estimate_pairs(g, k, p, seed)[1] for seed in range(1, S + 1)])
+    assert abs(ests.mean() - exact) <= 4.0 * ests.std(ddof=1) / np.sqrt(S) + 1e-9
