@@ -170,6 +170,9 @@ __device__ __forceinline__ uint32_t leaf2_rep(uint32_t C, int Wd, const uint32_t
     uint32_t Cr[WM];
 #pragma unroll
     for (int w = 0; w < WM; ++w) Cr[w] = __shfl_sync(kFull, C, w);
+    // 128-bit groups where C is non-zero (warp-uniform)
+    const uint32_t nz = __ballot_sync(kFull, lane < WM && C != 0u);
+    const int glo = nz ? (__ffs(nz) - 1) >> 2 : 0, ghi = nz ? (31 - __clz(nz)) >> 2 : -1;
     const uint32_t pc = (uint32_t)__popc(C);
     uint32_t pre = pc;
 #pragma unroll
@@ -197,6 +200,7 @@ __device__ __forceinline__ uint32_t leaf2_rep(uint32_t C, int Wd, const uint32_t
                 const uint4* A4 = (const uint4*)(A + (int64_t)e * RS);
 #pragma unroll
                 for (int q = 0; q < WM / 4; ++q) {
+                    if (q < glo || q > ghi) continue;
                     const uint4 a = A4[q];
                     f += (uint32_t)(__popc(Cr[4 * q] & a.x) + __popc(Cr[4 * q + 1] & a.y) +
                                     __popc(Cr[4 * q + 2] & a.z) + __popc(Cr[4 * q + 3] & a.w));
@@ -240,6 +244,11 @@ __device__ unsigned long long penult3(uint32_t C, int Wd, const uint32_t* A, int
 {
     if (lane < WM) sC[lane] = C;
     __syncwarp();
+    // 128-bit groups of words where C (hence every Ce) can be non-zero: the
+    // same for the whole warp, so the row loops skip the rest uniformly
+    const uint32_t nz = __ballot_sync(kFull, lane < WM && C != 0u);
+    if (nz == 0u) return 0ull;
+    const int glo = (__ffs(nz) - 1) >> 2, ghi = (31 - __clz(nz)) >> 2;
     const uint32_t pc = (uint32_t)__popc(C);
     uint32_t pre = pc;
 #pragma unroll
@@ -269,6 +278,10 @@ __device__ unsigned long long penult3(uint32_t C, int Wd, const uint32_t* A, int
             const uint4* C4 = (const uint4*)sC;
 #pragma unroll
             for (int q = 0; q < WM / 4; ++q) {
+                if (q < glo || q > ghi) {
+                    Ce[4 * q] = Ce[4 * q + 1] = Ce[4 * q + 2] = Ce[4 * q + 3] = 0u;
+                    continue;
+                }
                 const uint4 a = Ae4[q], cc4 = C4[q];
                 Ce[4 * q] = cc4.x & a.x;
                 Ce[4 * q + 1] = cc4.y & a.y;
@@ -286,6 +299,7 @@ __device__ unsigned long long penult3(uint32_t C, int Wd, const uint32_t* A, int
                     uint32_t dgr = 0;
 #pragma unroll
                     for (int r = 0; r < WM / 4; ++r) {
+                        if (r < glo || r > ghi) continue;
                         const uint4 a = F4[r];
                         dgr += (uint32_t)(__popc(Ce[4 * r] & a.x) + __popc(Ce[4 * r + 1] & a.y) +
                                           __popc(Ce[4 * r + 2] & a.z) + __popc(Ce[4 * r + 3] & a.w));
