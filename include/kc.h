@@ -260,6 +260,9 @@ kc_status kc_count_batch(const kc_graph* const* gs, int ng, int k, unsigned flag
  *   KC_PARAM_COMPACT_LO, KC_PARAM_COMPACT_HI  candidate sets of the ordered
  *       search with LO..HI elements (HI <= 64, default 1..64; HI = 0 off) are
  *       finished on a compact register copy of their induced subgraph.
+ *   KC_PARAM_TRI  1 (default): exact k = 3 counts take the triangle path --
+ *       each y of Gamma+(x_i) found in Gamma+(u) is counted directly (node
+ *       iterator, no G+(u) bitmap); 0: the bitmap path used for larger k.
  * kc_set_param returns KC_EINVAL for an unknown knob or a value out of range.
  */
 #define KC_PARAM_SMEM_MAX_WORDS 1
@@ -268,6 +271,7 @@ kc_status kc_count_batch(const kc_graph* const* gs, int ng, int k, unsigned flag
 #define KC_PARAM_ALGO           4
 #define KC_PARAM_COMPACT_LO     5
 #define KC_PARAM_COMPACT_HI     6
+#define KC_PARAM_TRI            7
 #define KC_ALGO_PIVOT 0
 #define KC_ALGO_DFS   1
 kc_status kc_set_param(int param, int64_t value);

@@ -51,6 +51,7 @@ int64_t sct_heavy_words_w(int W, int k, int64_t nheavy);
 kc_status sct_launch_slot(int slot, int Wh, const cc::Ctx& c, bool pv, bool col, uint32_t* heavy,
                           int64_t heavy_words, cudaStream_t s);
 bool dfs_reg_supported(int k);
+kc_status tri_launch_slot(int slot, int Wh, const cc::Ctx& c, bool pv, cudaStream_t s);
 kc_status dfs_reg_launch(const cc::Ctx& c, int W, bool pv, bool col, cudaStream_t s);
 
 kc_status set_smem_max_words(int64_t v)
@@ -477,6 +478,7 @@ kc_status launch_slot_dfs(int slot, int Wh, const Ctx& c, uint32_t* heavy, int64
 kc_status launch_slot(int slot, int Wh, const Ctx& c, bool pv, bool col, uint32_t* heavy, int64_t heavy_words,
                       cudaStream_t s)
 {
+    if (c.k == 3 && !col && tri_enabled()) return tri_launch_slot(slot, Wh, c, pv, s);  // no bitmaps for k = 3
     if (count_algo() == KC_ALGO_PIVOT) return sct_launch_slot(slot, Wh, c, pv, col, heavy, heavy_words, s);
     if (pv) {
         if (col) return KC_ENOTSUP;

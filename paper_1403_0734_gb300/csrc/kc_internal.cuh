@@ -140,6 +140,8 @@ int compact_hi();
 kc_status set_compact_window(int64_t lo, int64_t hi);
 int count_algo();
 kc_status set_count_algo(int64_t v);
+int tri_enabled();
+kc_status set_tri(int64_t v);
 
 // Words of global scratch the heavy (global-bitmap) class needs for k under
 // the current settings; *slot_words receives the size of one tile slot.

@@ -26,6 +26,7 @@ KC_PARAM_WORK_COUNT = 3
 KC_PARAM_ALGO = 4
 KC_PARAM_COMPACT_LO = 5
 KC_PARAM_COMPACT_HI = 6
+KC_PARAM_TRI = 7
 KC_ALGO_PIVOT = 0
 KC_ALGO_DFS = 1
 

@@ -88,3 +88,9 @@ def test_params(lib):
     kc.set_param(kc.KC_PARAM_ALGO, kc.KC_ALGO_DFS)
     with pytest.raises(kc.KcError):
         kc.set_param(kc.KC_PARAM_ALGO, 7)
+    assert kc.get_param(kc.KC_PARAM_TRI) == 1
+    kc.set_param(kc.KC_PARAM_TRI, 0)
+    assert kc.get_param(kc.KC_PARAM_TRI) == 0
+    kc.set_param(kc.KC_PARAM_TRI, 1)
+    with pytest.raises(kc.KcError):
+        kc.set_param(kc.KC_PARAM_TRI, 2)

@@ -244,6 +244,25 @@ def test_estimate_pairs_edges_and_tiles(kc):
         kc.set_param(kc.KC_PARAM_SMEM_MAX_WORDS, 32)
 
 
+@pytest.mark.parametrize("name", ["er_1000", "chunglu_20k", "sbm_20k", "rmat_s14", "chunglu_50k"])
+@pytest.mark.parametrize("maxw", [32, 1])
+def test_triangle_path_matches_oracle(kc, name, maxw):
+    """k = 3 through the triangle path (no bitmaps) and through the bitmap
+    path: totals, memberships and owner counts equal the oracle's.  n = 50000
+    has owners whose Gamma+ spans more ranks than the direct table holds;
+    maxw = 1 sends every owner wider than 32 to the widest-owner slot."""
+    g = graph(name)
+    G = kc.orient(g.off, g.adj)
+    kc.set_param(kc.KC_PARAM_SMEM_MAX_WORDS, maxw)
+    try:
+        for tri in (1, 0):
+            kc.set_param(kc.KC_PARAM_TRI, tri)
+            check_count(kc, g, G, 3)
+    finally:
+        kc.set_param(kc.KC_PARAM_TRI, 1)
+        kc.set_param(kc.KC_PARAM_SMEM_MAX_WORDS, 32)
+
+
 # ------------------------------------------------------------ edge cases
 
 def test_edge_cases(kc):
