@@ -468,7 +468,7 @@ kc_status launch_slot_dfs(int slot, int Wh, const Ctx& c, uint32_t* heavy, int64
     const Layout lay = make_layout(W, W + 1, NW, levels, PV, COL);
     const size_t smem = (size_t)lay.total * 4;
     auto kern = k_count_cta<PV, COL, false>;
-    if (smem > 48 * 1024) KC_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    KC_CK(cc::allow_smem(kern, smem));
     const int grid = (int)std::min<int64_t>(c.nitems, (int64_t)sms * cc::blocks_per_sm(kern, NW * 32, smem));
     kern<<<grid, NW * 32, smem, s>>>(c, W, levels, nullptr, 0);
     KC_LAUNCHED();

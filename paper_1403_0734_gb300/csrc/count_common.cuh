@@ -181,15 +181,55 @@ __device__ __forceinline__ uint32_t lower_rows_w1(uint32_t up, int d, int lane)
     return low;
 }
 
+// Direct-address table over the rank span [lo, lo + 32 words) of Gamma+(u):
+// bit (y - lo) set iff y is in Gamma+(u), pre[w] = number of elements below
+// lo + 32 w, so y's local index is pre[w] + popc(bits[w] below y's bit).
+// words == 0: no table (the span is too wide); searches fall back to binary
+// search in sL.
+struct SpanTable {
+    uint32_t* bits;
+    uint16_t* pre;
+    int32_t lo;
+    int words;
+};
+
+// Fill T for sL[0..d) (ascending) by the threads of the CTA when the span
+// fits maxw words; ends with __syncthreads().  Every thread must call it.
+__device__ __forceinline__ void span_table_build(SpanTable& T, const int32_t* sL, int d, int maxw)
+{
+    const int64_t span = (int64_t)sL[d - 1] - sL[0] + 1;
+    T.lo = sL[0];
+    T.words = span <= 32LL * maxw ? (int)((span + 31) >> 5) : 0;
+    if (T.words == 0) return;
+    for (int w = threadIdx.x; w < T.words; w += blockDim.x) T.bits[w] = 0u;
+    __syncthreads();
+    for (int j = threadIdx.x; j < d; j += blockDim.x) {
+        const int off = sL[j] - T.lo;
+        atomicOr(&T.bits[off >> 5], 1u << (off & 31));
+    }
+    for (int w = threadIdx.x; w < T.words; w += blockDim.x) {
+        const int32_t key = T.lo + 32 * w;
+        int a = 0, z = d;
+        while (a < z) {
+            const int mid = (a + z) >> 1;
+            if (sL[mid] < key) a = mid + 1; else z = mid;
+        }
+        T.pre[w] = (uint16_t)a;
+    }
+    __syncthreads();
+}
+
 // Rows of G+(u) into a bitmap A (row stride RS words, zeroed beforehand) by
 // warps w0, w0+nw, ... of the caller; sL holds Gamma+(u) (ranks, ascending),
 // sCol their sampling labels (COL; ur: u's original id).  With SYM the
 // bitmap is made symmetric.
 template <bool SYM, bool COL>
 __device__ __forceinline__ void build_rows(const Ctx& c, const int32_t* sL, const uint32_t* sCol, int d,
-                                           uint32_t* A, int RS, int w0, int nw, int lane, int32_t ur = 0)
+                                           uint32_t* A, int RS, int w0, int nw, int lane, int32_t ur = 0,
+                                           const SpanTable* T = nullptr)
 {
     const int32_t maxL = sL[d - 1];
+    const bool direct = T && T->words > 0;
     for (int i = w0; i < d - 1; i += nw) {
         const int32_t xi = sL[i];
         const int64_t s0 = c.offp[xi], s1 = c.offp[xi + 1];
@@ -198,12 +238,22 @@ __device__ __forceinline__ void build_rows(const Ctx& c, const int32_t* sL, cons
             const int64_t pp = p0 + lane;
             const int32_t y = pp < s1 ? c.adjp[pp] : INT_MAX;
             if (y <= maxL) {
-                int lo = i + 1, hi = d;
-                while (lo < hi) {
-                    const int mid = (lo + hi) >> 1;
-                    if (sL[mid] < y) lo = mid + 1; else hi = mid;
+                int lo = i + 1;
+                bool hit;
+                if (direct) {  // y > x_i >= lo: inside the span
+                    const int off = y - T->lo;
+                    const uint32_t wv = T->bits[off >> 5];
+                    hit = (wv >> (off & 31)) & 1u;
+                    lo = (int)T->pre[off >> 5] + __popc(wv & mask_below(off & 31));
+                } else {
+                    int hi = d;
+                    while (lo < hi) {
+                        const int mid = (lo + hi) >> 1;
+                        if (sL[mid] < y) lo = mid + 1; else hi = mid;
+                    }
+                    hit = lo < d && sL[lo] == y;
                 }
-                if (lo < d && sL[lo] == y && (!COL || sample_keep(c, ur, ci, sCol[lo]))) {
+                if (hit && (!COL || sample_keep(c, ur, ci, sCol[lo]))) {
                     atomicOr(&A[(int64_t)i * RS + (lo >> 5)], 1u << (lo & 31));
                     if (SYM) atomicOr(&A[(int64_t)lo * RS + (i >> 5)], 1u << (i & 31));
                 }
@@ -211,6 +261,16 @@ __device__ __forceinline__ void build_rows(const Ctx& c, const int32_t* sL, cons
             if (__shfl_sync(kFull, y, 31) >= maxL) break;
         }
     }
+}
+
+// Opt a kernel in to `smem` bytes of dynamic shared memory.  The default
+// limit (48 KB) covers static and dynamic shared memory together, so the
+// attribute is set whenever the dynamic part alone comes near it.
+template <typename K>
+inline cudaError_t allow_smem(K kernel, size_t smem)
+{
+    if (smem <= 32 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
 template <typename K>

@@ -60,8 +60,10 @@ kc_status set_compact_window(int64_t lo, int64_t hi)
 namespace {
 
 struct RLayout {
-    int64_t L, col, pvlo, pvhi, A, total;
+    int64_t L, col, pvlo, pvhi, A, sbits, spre, total;
 };
+
+constexpr int kSpanWords = 1024;  // direct table of the build: spans up to 32768 ranks
 
 __host__ __device__ inline RLayout make_rlayout(int W, int RS, bool pv, bool col, int NW = 0)
 {
@@ -72,7 +74,9 @@ __host__ __device__ inline RLayout make_rlayout(int W, int RS, bool pv, bool col
     l.pvlo = l.col + (col ? D : 0);
     l.pvhi = l.pvlo + (pv ? D : 0);
     l.A = l.pvhi + (pv ? D : 0);
-    l.total = l.A + D * RS;
+    l.sbits = l.A + D * RS;
+    l.spre = l.sbits + kSpanWords;
+    l.total = l.spre + kSpanWords / 2;
     (void)NW;
     return l;
 }
@@ -584,7 +588,9 @@ __global__ void __launch_bounds__(256, 4) k_dfs_reg(Ctx cb, int W, int R, int cl
             s_wk = 0ull;
         }
         __syncthreads();
-        cc::build_rows<PV, COL>(c, sL, sCol, d, sA, RS, wid, NW, lane, ur);
+        cc::SpanTable T{smem + lay.sbits, (uint16_t*)(smem + lay.spre), 0, 0};
+        cc::span_table_build(T, sL, d, kSpanWords);
+        cc::build_rows<PV, COL>(c, sL, sCol, d, sA, RS, wid, NW, lane, ur, &T);
         __syncthreads();
 
         unsigned long long wtot = 0, wk = 0;
@@ -677,8 +683,7 @@ kc_status dfs_reg_launch(const cc::Ctx& c, int W, bool pv, bool col, cudaStream_
     const RLayout lay = make_rlayout(W, row_stride(W, WM), pv, col, NW);
     const size_t smem = (size_t)lay.total * 4;
     auto pick = [&](auto kern) -> kc_status {
-        if (smem > 48 * 1024)
-            KC_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        KC_CK(cc::allow_smem(kern, smem));
         const int grid =
             (int)std::min<int64_t>(c.nitems * R, (int64_t)sms * cc::blocks_per_sm(kern, NW * 32, smem));
         kern<<<grid, NW * 32, smem, s>>>(c, W, R, g_compact_lo, g_compact_hi);

@@ -498,7 +498,7 @@ kc_status launch_slot_sct(int slot, int Wh, const Ctx& c, uint32_t* heavy, int64
     const int NW = (int)std::max<size_t>(1, std::min<size_t>(8, (size_t)(100 * 1024) / per_warp));
     const size_t smem = per_warp * NW;
     auto kern = k_sct_warp<PV, COL, false>;
-    if (smem > 48 * 1024) KC_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    KC_CK(cc::allow_smem(kern, smem));
     const int64_t ctas = (c.nitems + NW - 1) / NW;
     const int grid = (int)std::min<int64_t>(ctas, (int64_t)sms * cc::blocks_per_sm(kern, NW * 32, smem));
     kern<<<grid, NW * 32, smem, s>>>(c, W, nullptr, 0);

@@ -9,7 +9,7 @@
 //     registers (lane j holds x_j), every entry y of a 32-entry chunk of
 //     Gamma+(x_i) located by a shuffle binary search;
 //   * wider owners: one CTA per owner, Gamma+(u) in shared memory, and when
-//     its rank span max - min + 1 is at most kSpanBits a direct-address
+//     its rank span max - min + 1 is at most 32 kSpanWords a direct-address
 //     table over the span -- a bitmap with a per-word prefix count -- so
 //     that membership and local index of y cost two independent shared loads
 //     instead of a dependent binary search.
@@ -32,7 +32,6 @@ using cc::Ctx;
 using cc::mask_below;
 
 constexpr int kSpanWords = 1024;                // direct table: spans up to 32768 ranks
-constexpr int kSpanBits = kSpanWords * 32;
 constexpr int kWarpItems = 4;                    // owners a warp takes per cursor step
 
 // --------------------------------------------------------- d+ <= 32
@@ -90,8 +89,8 @@ __global__ void __launch_bounds__(256) k_tri_warp(Ctx cb)
 
 // ---------------------------------------------------------- d+ > 32
 
-// Shared layout (32-bit words): sL[D] ranks, sCnt[D] memberships (PV),
-// sBits[kSpanWords] span bitmap, sPre[kSpanWords] prefix counts.
+// Shared layout (32-bit words): sL[D] ranks, sCnt[D] memberships (PV), the
+// span table's bitmap (kSpanWords) and 16-bit prefix counts (kSpanWords / 2).
 template <bool PV>
 __global__ void __launch_bounds__(256) k_tri_cta(Ctx cb, int D)
 {
@@ -99,7 +98,7 @@ __global__ void __launch_bounds__(256) k_tri_cta(Ctx cb, int D)
     int32_t* sL = (int32_t*)smem;
     uint32_t* sCnt = smem + D;
     uint32_t* sBits = sCnt + (PV ? D : 0);
-    uint32_t* sPre = sBits + kSpanWords;
+    uint16_t* sPre = (uint16_t*)(sBits + kSpanWords);
     __shared__ unsigned long long s_tot;
     __shared__ long long s_item;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, NW = blockDim.x >> 5;
@@ -121,28 +120,9 @@ __global__ void __launch_bounds__(256) k_tri_cta(Ctx cb, int D)
         }
         __syncthreads();
         const int32_t lo = sL[0], maxL = sL[d - 1];
-        const int64_t span = (int64_t)maxL - lo + 1;
-        const bool direct = span <= kSpanBits;
-        const int sw = direct ? (int)((span + 31) >> 5) : 0;
-        if (direct) {
-            for (int w = threadIdx.x; w < sw; w += blockDim.x) sBits[w] = 0u;
-            __syncthreads();
-            for (int j = threadIdx.x; j < d; j += blockDim.x) {
-                const int off = sL[j] - lo;
-                atomicOr(&sBits[off >> 5], 1u << (off & 31));
-            }
-            // sPre[w] = number of elements below lo + 32 w (lower bound in sL)
-            for (int w = threadIdx.x; w < sw; w += blockDim.x) {
-                const int32_t key = lo + 32 * w;
-                int a = 0, z = d;
-                while (a < z) {
-                    const int mid = (a + z) >> 1;
-                    if (sL[mid] < key) a = mid + 1; else z = mid;
-                }
-                sPre[w] = (uint32_t)a;
-            }
-        }
-        __syncthreads();
+        cc::SpanTable T{sBits, sPre, 0, 0};
+        cc::span_table_build(T, sL, d, kSpanWords);
+        const bool direct = T.words > 0;
 
         unsigned long long wtot = 0;
         for (int i = wid; i < d - 1; i += NW) {
@@ -221,9 +201,9 @@ kc_status tri_launch_slot(int slot, int Wh, const cc::Ctx& c, bool pv, cudaStrea
     }
     const int W = slot == 0 ? Wh : slot_words(slot);
     const int D = 32 * W;
-    const size_t smem = (size_t)(D * (pv ? 2 : 1) + 2 * kSpanWords) * 4;
+    const size_t smem = (size_t)(D * (pv ? 2 : 1) + kSpanWords + kSpanWords / 2) * 4;
     auto kern = pv ? k_tri_cta<true> : k_tri_cta<false>;
-    if (smem > 48 * 1024) KC_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    KC_CK(cc::allow_smem(kern, smem));
     const int grid = (int)std::min<int64_t>(c.nitems, (int64_t)sms * cc::blocks_per_sm(kern, 256, smem));
     kern<<<grid, 256, smem, s>>>(c, D);
     KC_LAUNCHED();
