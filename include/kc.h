@@ -49,7 +49,8 @@ typedef enum {
     KC_EOVERFLOW = 3,  /* a count exceeded 2^64 - 1 */
     KC_ETIMEOUT = 4,   /* a bounded device-side wait gave up */
     KC_ECUDA = 5,      /* a CUDA runtime call failed (see kc_last_cuda_error) */
-    KC_ENOTSUP = 6     /* request outside the supported range */
+    KC_ENOTSUP = 6,    /* request outside the supported range */
+    KC_ECANCELED = 7   /* a caller's callback asked to stop */
 } kc_status;
 
 /* flags */
@@ -198,6 +199,32 @@ kc_status kc_estimate(const kc_graph* g, int k, uint32_t colours, uint64_t seed,
 kc_status kc_estimate_pairs(const kc_graph* g, int k, double p, uint64_t seed,
                             unsigned flags, uint64_t* sampled, double* estimate,
                             uint64_t* per_owner, void* stream);
+
+/*
+ * kc_list -- k-clique listing (the exact algorithm lists as well as counts,
+ * Sec. 1; Reduce 3 of Sec. 3 enumerates the (k-1)-cliques of every G+(u)).
+ * Every k-clique of G is delivered exactly once, as k caller ids ordered by
+ * the total order of Sec. 2 (its smallest vertex, the owner u, first), in
+ * runs of at most `cap` cliques: the library fills `buf` (cap * k int32,
+ * row-major, one clique per row) with a run, then calls
+ * fn(user, buf, count) on the calling thread with the run complete; after fn
+ * returns the buffer is reused.  A run holds the cliques of consecutive
+ * owners of the work queue, so the order of runs and of rows inside a run is
+ * deterministic but unspecified.
+ *   k        1..KC_MAX_K (k = 1: every vertex; k = 2: every edge)
+ *   buf      host buffer, or with KC_DEVICE_PTRS a device buffer (fn then
+ *            receives the device pointer; the run is complete on `stream`)
+ *   cap      >= the largest per-owner count q_{u,k-1} (kc_count's per_owner
+ *            output); a smaller cap returns KC_ENOMEM before anything is
+ *            delivered from that owner
+ *   fn       non-NULL; a non-zero return stops the listing (KC_ECANCELED)
+ *   listed   out, host: number of cliques delivered to fn so far
+ * Errors: KC_EINVAL (bad k, cap < 1, NULL argument), KC_ENOMEM, KC_ECANCELED,
+ * KC_ECUDA.
+ */
+typedef int (*kc_list_fn)(void* user, const int32_t* cliques, int64_t count);
+kc_status kc_list(const kc_graph* g, int k, unsigned flags, int32_t* buf, int64_t cap,
+                  kc_list_fn fn, void* user, uint64_t* listed, void* stream);
 
 /*
  * kc_footprint -- device memory a kc_count / kc_estimate call on g for k

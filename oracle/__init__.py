@@ -65,6 +65,9 @@ def _load():
     lib.oracle_fff_pairs.restype = ctypes.c_int
     lib.oracle_owner_pairs.argtypes = [P, P, ctypes.c_int32, ctypes.c_int, P, U64P, U64P]
     lib.oracle_owner_pairs.restype = ctypes.c_int
+    lib.oracle_list.argtypes = [P, P, ctypes.c_int32, ctypes.c_int, P, ctypes.c_int64,
+                                ctypes.POINTER(ctypes.c_int64)]
+    lib.oracle_list.restype = ctypes.c_int
     lib.oracle_brute_force.argtypes = [P, P, ctypes.c_int32, ctypes.c_int, U64P, U64P, P]
     lib.oracle_brute_force.restype = ctypes.c_int
     lib.oracle_max_threads.argtypes = [ctypes.c_int]
@@ -208,6 +211,18 @@ def owner_pairs(g, u: int, k: int, kept) -> int:
     _check(_load().oracle_owner_pairs(off.ctypes.data, adj.ctypes.data, u, k, kept.ctypes.data,
                                       ctypes.byref(lo), ctypes.byref(hi)))
     return (int(hi.value) << 64) | int(lo.value)
+
+
+def list_cliques(g, k: int) -> np.ndarray:
+    """Every k-clique as a row of k ids in precedence order, owner first
+    (Reduce 3's enumeration, Sec. 3); rows in owner-id order."""
+    off, adj = _csr(g)
+    cnt = ctypes.c_int64(0)
+    _check(_load().oracle_list(off.ctypes.data, adj.ctypes.data, g.n, k, None, 0, ctypes.byref(cnt)))
+    out = np.zeros((max(cnt.value, 1), k), dtype=np.int32)
+    _check(_load().oracle_list(off.ctypes.data, adj.ctypes.data, g.n, k, out.ctypes.data, cnt.value,
+                               ctypes.byref(cnt)))
+    return out[: cnt.value]
 
 
 def brute_force(g, k: int, per_vertex: bool = False):

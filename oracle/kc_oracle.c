@@ -173,6 +173,9 @@ typedef struct {
     int32_t u;
     uint64_t* per_vertex;  /* nullable: membership counts, atomically updated */
     int overflow;
+    int listing;           /* enumerate the cliques (count them in list_n) */
+    int32_t* list;         /* nullable: listing output, k ids per clique */
+    int64_t list_cap, list_n;
 } rec_ctx;
 
 static void add_u64(uint64_t* p, uint64_t v, int* overflow)
@@ -192,6 +195,15 @@ static void add_u64(uint64_t* p, uint64_t v, int* overflow)
 static u128 count_rec(rec_ctx* c, const int32_t* cand, int32_t ncand, int s)
 {
     if (s == c->k - 1) {
+        if (c->listing) {  /* listing: u, the chain, then each candidate */
+            for (int32_t i = 0; i < ncand; ++i, ++c->list_n) {
+                if (!c->list || c->list_n >= c->list_cap) continue;
+                int32_t* row = c->list + c->list_n * c->k;
+                row[0] = c->u;
+                for (int t = 0; t < s - 1; ++t) row[1 + t] = c->L[c->chain[t]];
+                row[c->k - 1] = c->L[cand[i]];
+            }
+        }
         if (c->per_vertex && ncand > 0) {
             add_u64(&c->per_vertex[c->u], (uint64_t)ncand, &c->overflow);
             for (int t = 0; t < s - 1; ++t)
@@ -237,8 +249,19 @@ typedef struct {
     const uint8_t* given_kept;    /* explicit emitted pairs (d+ x d+, row i, column j > i), or NULL */
 } sampler;
 
+static int owner_work_list(const int64_t* off, const int32_t* adj, int32_t u, int k,
+                           const sampler* sm, uint64_t* per_vertex, u128* q_u,
+                           int32_t* list, int64_t list_cap, int64_t* list_n);
+
 static int owner_work(const int64_t* off, const int32_t* adj, int32_t u, int k,
                       const sampler* sm, uint64_t* per_vertex, u128* q_u)
+{
+    return owner_work_list(off, adj, u, k, sm, per_vertex, q_u, NULL, 0, NULL);
+}
+
+static int owner_work_list(const int64_t* off, const int32_t* adj, int32_t u, int k,
+                           const sampler* sm, uint64_t* per_vertex, u128* q_u,
+                           int32_t* list, int64_t list_cap, int64_t* list_n)
 {
     uint32_t colours = sm->colours;
     uint64_t seed = sm->seed;
@@ -280,8 +303,9 @@ static int owner_work(const int64_t* off, const int32_t* adj, int32_t u, int k,
         }
     }
     for (int32_t i = 0; i < dp; ++i) all[i] = i;
-    rec_ctx c = { k, L, out, outlen, chain, u, per_vertex, 0 };
+    rec_ctx c = { k, L, out, outlen, chain, u, per_vertex, 0, list_n != NULL, list, list_cap, list_n ? *list_n : 0 };
     *q_u = count_rec(&c, all, dp, 1);                            /* Reduce 3 */
+    if (list_n) *list_n = c.list_n;
     if (c.overflow < 0) st = OR_ENOMEM;
     else if (c.overflow) st = OR_OVERFLOW;
 done:
@@ -417,6 +441,42 @@ double oracle_scale_estimate(uint64_t sampled, uint32_t colours, int k)
     double f = 1.0;
     for (int i = 0; i < k - 2; ++i) f *= (double)colours;
     return (double)sampled * f;
+}
+
+/* ------------------------------------------------------- listing */
+
+/* Every k-clique once (Reduce 3 enumerates the (k-1)-cliques of each G+(u),
+ * Sec. 3), as k ids in precedence order, owner first: k = 1 lists every
+ * vertex, k = 2 every edge (u, x) with u preceding x.  Owners in id order,
+ * single-threaded.  Writes at most cap rows; *count receives the number of
+ * cliques (which may exceed cap). */
+int oracle_list(const int64_t* off, const int32_t* adj, int32_t n, int k,
+                int32_t* out, int64_t cap, int64_t* count)
+{
+    if (n < 0 || k < 1 || cap < 0) return OR_EINVAL;
+    int64_t nl = 0;
+    for (int32_t u = 0; u < n; ++u) {
+        if (k == 1) {
+            if (nl < cap) out[nl] = u;
+            ++nl;
+            continue;
+        }
+        if (k == 2) {
+            for (int64_t p = off[u]; p < off[u + 1]; ++p) {
+                int32_t x = adj[p];
+                if (!precedes(off, u, x)) continue;
+                if (nl < cap) { out[2 * nl] = u; out[2 * nl + 1] = x; }
+                ++nl;
+            }
+            continue;
+        }
+        sampler sm = { 0, 0, NULL, 0, 0, NULL };
+        u128 q = 0;
+        int st = owner_work_list(off, adj, u, k, &sm, NULL, &q, out, cap, &nl);
+        if (st != OR_OK) return st;
+    }
+    *count = nl;
+    return OR_OK;
 }
 
 /* ------------------------------------------------------- brute force */

@@ -54,44 +54,7 @@ int grid1d(int64_t n)
     return (int)(g < 1 ? 1 : g);
 }
 
-// Stream-ordered scratch, released on scope exit (after the stream's work).
-struct Scratch {
-    cudaStream_t s;
-    std::vector<void*> ptrs;
-    explicit Scratch(cudaStream_t st) : s(st) {}
-    ~Scratch()
-    {
-        for (void* p : ptrs) cudaFreeAsync(p, s);
-    }
-    template <typename T>
-    kc_status get(T** p, int64_t count)
-    {
-        void* q = nullptr;
-        cudaError_t e = cudaMallocAsync(&q, (size_t)std::max<int64_t>(count, 1) * sizeof(T), s);
-        if (e != cudaSuccess) {
-            set_cuda_error(e, "cudaMallocAsync");
-            return e == cudaErrorMemoryAllocation ? KC_ENOMEM : KC_ECUDA;
-        }
-        ptrs.push_back(q);
-        *p = (T*)q;
-        return KC_OK;
-    }
-};
 
-struct DeviceGuard {
-    int prev = -1;
-    explicit DeviceGuard(int dev)
-    {
-        cudaGetDevice(&prev);
-        if (prev != dev) cudaSetDevice(dev);
-    }
-    ~DeviceGuard()
-    {
-        int cur = -1;
-        cudaGetDevice(&cur);
-        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
-    }
-};
 
 // Host-ordered output of an n-array: device array `src` -> `dst` (host or
 // device per `dev`).
@@ -222,6 +185,7 @@ const char* kc_strerror(kc_status s)
     case KC_ETIMEOUT: return "device wait timed out";
     case KC_ECUDA: return "CUDA error";
     case KC_ENOTSUP: return "not supported";
+    case KC_ECANCELED: return "stopped by the callback";
     }
     return "unknown status";
 }
@@ -349,6 +313,14 @@ kc_status kc_estimate_pairs(const kc_graph* g, int k, double p, uint64_t seed, u
         *estimate = (double)*sampled / f;
     }
     return KC_OK;
+}
+
+kc_status kc_list(const kc_graph* g, int k, unsigned flags, int32_t* buf, int64_t cap, kc_list_fn fn, void* user,
+                  uint64_t* listed, void* stream)
+{
+    if (!g || !buf || !fn || !listed || k < 1 || k > KC_MAX_K || cap < 1) return KC_EINVAL;
+    kc::DeviceGuard dg(g->device);
+    return kc::list_run(g, k, flags, buf, cap, fn, user, listed, (cudaStream_t)stream);
 }
 
 kc_status kc_footprint(const kc_graph* g, int k, int per_vertex, int per_owner, int host_outputs,

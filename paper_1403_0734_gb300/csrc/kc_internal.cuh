@@ -1,6 +1,7 @@
 // kc_internal.cuh -- internal declarations of libkc (not part of the ABI).
 #pragma once
 
+#include <algorithm>
 #include <cstdint>
 #include <cstddef>
 #include <vector>
@@ -140,8 +141,49 @@ int compact_hi();
 kc_status set_compact_window(int64_t lo, int64_t hi);
 int count_algo();
 kc_status set_count_algo(int64_t v);
+kc_status list_run(const kc_graph* g, int k, unsigned flags, int32_t* buf, int64_t cap, kc_list_fn fn, void* user,
+                   uint64_t* listed, cudaStream_t s);
 int tri_enabled();
 kc_status set_tri(int64_t v);
+
+// Stream-ordered scratch, released on scope exit (after the stream's work).
+struct Scratch {
+    cudaStream_t s;
+    std::vector<void*> ptrs;
+    explicit Scratch(cudaStream_t st) : s(st) {}
+    ~Scratch()
+    {
+        for (void* p : ptrs) cudaFreeAsync(p, s);
+    }
+    template <typename T>
+    kc_status get(T** p, int64_t count)
+    {
+        void* q = nullptr;
+        cudaError_t e = cudaMallocAsync(&q, (size_t)std::max<int64_t>(count, 1) * sizeof(T), s);
+        if (e != cudaSuccess) {
+            set_cuda_error(e, "cudaMallocAsync");
+            return e == cudaErrorMemoryAllocation ? KC_ENOMEM : KC_ECUDA;
+        }
+        ptrs.push_back(q);
+        *p = (T*)q;
+        return KC_OK;
+    }
+};
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
 
 // Words of global scratch the heavy (global-bitmap) class needs for k under
 // the current settings; *slot_words receives the size of one tile slot.

@@ -16,7 +16,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libkc.so")
 
-KC_OK, KC_EINVAL, KC_ENOMEM, KC_EOVERFLOW, KC_ETIMEOUT, KC_ECUDA, KC_ENOTSUP = range(7)
+KC_OK, KC_EINVAL, KC_ENOMEM, KC_EOVERFLOW, KC_ETIMEOUT, KC_ECUDA, KC_ENOTSUP, KC_ECANCELED = range(8)
 KC_DEVICE_PTRS = 0x1
 KC_VALIDATE = 0x2
 KC_MAX_K = 32
@@ -81,6 +81,9 @@ def _load():
     lib.kc_estimate_pairs.argtypes = [_P, ctypes.c_int, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint, _P, _P, _P,
                                       _P]
     lib.kc_estimate_pairs.restype = st
+    lib.kc_list.argtypes = [_P, ctypes.c_int, ctypes.c_uint, _P, ctypes.c_int64, LIST_FN, _P,
+                            ctypes.POINTER(ctypes.c_uint64), _P]
+    lib.kc_list.restype = st
     lib.kc_count_csr.argtypes = [_P, _P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int, ctypes.c_uint, _P, _P, _P, _P]
     lib.kc_count_csr.restype = st
     lib.kc_estimate_csr.argtypes = [_P, _P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int, ctypes.c_uint32,
@@ -297,6 +300,44 @@ def estimate_pairs(g: Graph, k: int, p: float, seed: int, per_owner: bool = Fals
     _check(_load().kc_estimate_pairs(g.handle, k, float(p), seed, 0, ctypes.byref(s), ctypes.byref(est), _ptr(po),
                                      _stream_handle(stream)), f"kc_estimate_pairs(k={k}, p={p})")
     return int(s.value), float(est.value), (po[: g.n] if po is not None else None)
+
+
+LIST_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64)
+
+
+def list_runs(g: Graph, k: int, fn, cap: int = 1 << 20, device_buffer=None, stream=None) -> int:
+    """k-clique listing (kc_list): fn(rows) is called once per run with the
+    run's cliques -- a host numpy view (count, k) of int32 caller ids in
+    precedence order, owner first, valid only during the call -- or, with
+    device_buffer (a CUDA tensor of cap * k int32), with (pointer, count).
+    fn returning a true value stops the listing (KcError KC_ECANCELED).
+    Returns the number of cliques delivered."""
+    flags = 0
+    if device_buffer is not None:
+        flags = KC_DEVICE_PTRS
+        buf_ptr = _ptr(device_buffer)
+        hbuf = None
+    else:
+        hbuf = np.empty((max(cap, 1), k), dtype=np.int32)
+        buf_ptr = hbuf.ctypes.data
+
+    def trampoline(_user, ptr, count):
+        if hbuf is not None:
+            return 1 if fn(hbuf[:count]) else 0
+        return 1 if fn((ptr, count)) else 0
+
+    cb = LIST_FN(trampoline)
+    listed = ctypes.c_uint64(0)
+    _check(_load().kc_list(g.handle, k, flags, buf_ptr, cap, cb, None, ctypes.byref(listed),
+                           _stream_handle(stream)), f"kc_list(k={k})")
+    return int(listed.value)
+
+
+def list_cliques(g: Graph, k: int, cap: int = 1 << 20, stream=None) -> np.ndarray:
+    """Every k-clique as rows of k caller ids (precedence order, owner first)."""
+    parts = []
+    list_runs(g, k, lambda rows: parts.append(rows.copy()), cap=cap, stream=stream)
+    return np.concatenate(parts) if parts else np.zeros((0, k), dtype=np.int32)
 
 
 def count_csr(off, adj, k: int, per_vertex: bool = False, per_owner: bool = False, validate: bool = False,

@@ -405,3 +405,82 @@ def test_batch_edge_cases(kc):
     G = kc.orient(np.zeros(1, np.int64), np.zeros(0, np.int32))
     H = kc.orient(kcgen.complete(40).off, kcgen.complete(40).adj)
     assert kc.count_batch([G, H, G], 5) == [0, comb(40, 5), 0]
+
+
+# ------------------------------------------------------------ listing (Sec. 3)
+
+def _rows(a):
+    """Rows as a lexicographically sorted array (for set comparison)."""
+    a = np.ascontiguousarray(a, dtype=np.int32)
+    if len(a) == 0:
+        return a
+    return a[np.lexsort(a.T[::-1])]
+
+
+def check_listing(kc, g, G, k, cap):
+    got = kc.list_cliques(G, k, cap=cap)
+    want = oracle.list_cliques(g, k)
+    assert got.shape == want.shape, (g.name, k, got.shape, want.shape)
+    # rows are unique and in precedence order with the owner first, on both sides
+    assert np.array_equal(_rows(got), _rows(want)), (g.name, k)
+
+
+@pytest.mark.parametrize("name,ks", [("er_1000", (1, 2, 3, 4)), ("chunglu_20k", (3, 4, 5)),
+                                     ("rmat_s12", (3, 4, 5)), ("sbm_20k", (4, 6))])
+def test_listing_matches_oracle(kc, name, ks):
+    g = graph(name)
+    G = kc.orient(g.off, g.adj)
+    for k in ks:
+        check_listing(kc, g, G, k, cap=1 << 22)
+
+
+def test_listing_small_runs_and_wide_owners(kc):
+    """Runs as small as the largest owner's count (many runs), owners in the
+    32-word class, and every owner above 32 in the widest-owner tiles."""
+    g = kcgen.random_small(700, 0.45, 1)
+    G = kc.orient(g.off, g.adj)
+    _, po, _ = oracle.count(g, 4, per_owner=True)
+    check_listing(kc, g, G, 4, cap=int(po.max()))
+    g2 = graph("rmat_s12")
+    G2 = kc.orient(g2.off, g2.adj)
+    kc.set_param(kc.KC_PARAM_SMEM_MAX_WORDS, 1)
+    try:
+        for k in (3, 4):
+            _, po2, _ = oracle.count(g2, k, per_owner=True)
+            check_listing(kc, g2, G2, k, cap=int(po2.max()) + 7)
+    finally:
+        kc.set_param(kc.KC_PARAM_SMEM_MAX_WORDS, 32)
+
+
+def test_listing_device_buffer_cancel_and_errors(kc):
+    import torch
+    g = graph("chunglu_20k")
+    G = kc.orient(g.off, g.adj)
+    k = 4
+    q, po, _ = oracle.count(g, k, per_owner=True)
+    cap = int(po.max()) * 3
+    buf = torch.empty(cap * k, dtype=torch.int32, device="cuda")
+    seen = []
+
+    def fn(arg):
+        ptr, count = arg
+        seen.append(buf[: count * k].view(count, k).cpu().numpy().copy())
+        return False
+
+    assert kc.list_runs(G, k, fn, cap=cap, device_buffer=buf) == q
+    assert len(seen) > 1
+    assert np.array_equal(_rows(np.concatenate(seen)), _rows(oracle.list_cliques(g, k)))
+    # the callback stops the listing after its first run
+    first = []
+    with pytest.raises(kc.KcError) as ei:
+        kc.list_runs(G, k, lambda rows: first.append(len(rows)) or True, cap=cap)
+    assert ei.value.status == kc.KC_ECANCELED and len(first) == 1
+    # a buffer smaller than one owner's cliques
+    with pytest.raises(kc.KcError) as ei:
+        kc.list_runs(G, k, lambda rows: False, cap=int(po.max()) - 1)
+    assert ei.value.status == kc.KC_ENOMEM
+    # empty graph, k above the clique number
+    G0 = kc.orient(np.zeros(1, np.int64), np.zeros(0, np.int32))
+    assert kc.list_cliques(G0, 3).shape == (0, 3)
+    ge = graph("er_1000")
+    assert kc.list_cliques(kc.orient(ge.off, ge.adj), 7).shape == (0, 7)

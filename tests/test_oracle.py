@@ -407,3 +407,27 @@ def test_pairs_mean_over_seeds():
     exact = oracle.count(g, k)[0]
     ests = np.array([oracle.estimate_pairs(g, k, p, seed)[1] for seed in range(1, S + 1)])
     assert abs(ests.mean() - exact) <= 4.0 * ests.std(ddof=1) / np.sqrt(S) + 1e-9
+
+
+# ------------------------------------------------------------ listing (Sec. 3)
+
+@pytest.mark.parametrize("seed", [3, 4, 5])
+def test_listing_matches_brute_force(seed):
+    """Every k-clique exactly once (as a set), each row in precedence order
+    with the owner first, the number of rows q_k."""
+    g = kcgen.random_small(25, 0.5, seed)
+    for k in (1, 2, 3, 4, 5, 6):
+        L = oracle.list_cliques(g, k)
+        assert len(L) == oracle.count(g, k)[0]
+        got = sorted(tuple(sorted(r)) for r in L.tolist())
+        assert got == sorted(py_cliques(g, k))
+        for r in L.tolist():
+            assert all(oracle.precedes(g, r[i], r[i + 1]) for i in range(k - 1))
+
+
+def test_listing_complete_graph():
+    g = kcgen.complete(12)
+    for k in (3, 5, 12):
+        L = oracle.list_cliques(g, k)
+        assert len(L) == comb(12, k)
+        assert len({tuple(sorted(r)) for r in L.tolist()}) == comb(12, k)
