@@ -200,6 +200,26 @@ def random_small(n: int, p: float, seed: int) -> Graph:
     return from_edges(n, np.stack([iu[keep], ju[keep]], axis=1), f"gnp_{n}_{p}_{seed}")
 
 
+def planted_core(n_bg: int, m_bg: int, core: int, p_core: float, seed: int, gamma: float = 2.1,
+                 wmax: float = 2000.0) -> Graph:
+    """A Chung-Lu power-law background (n_bg vertices, m_bg draws, exponent
+    gamma, max weight wmax) with a G(core, p_core) random graph planted on
+    `core` seeded-random vertices.  The planted vertices become hubs whose
+    high-neighbourhoods hold hundreds of vertices but only a fraction p_core
+    of the pairs, so clique counts stay moderate while |Gamma+| reaches the
+    widest bitmap classes (numpy Generator for the core; not a benchmark
+    input)."""
+    bg = chung_lu(n_bg, m_bg, gamma, wmax, seed)
+    rng = np.random.default_rng(seed)
+    ids = rng.choice(n_bg, core, replace=False)
+    iu, ju = np.triu_indices(core, 1)
+    keep = rng.random(iu.shape[0]) < p_core
+    src = np.repeat(np.arange(bg.n, dtype=np.int64), np.diff(bg.off))
+    e = np.concatenate([np.stack([src, bg.adj.astype(np.int64)], axis=1),
+                        np.stack([ids[iu[keep]], ids[ju[keep]]], axis=1)])
+    return from_edges(n_bg, e, f"planted_cl{n_bg}_core{core}_p{p_core}_s{seed}")
+
+
 # --- the five benchmark workloads -------------------------------------------
 
 def er_1000(seed: int = 1) -> Graph:

@@ -50,6 +50,8 @@ def _load():
                                ctypes.c_uint64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int,
                                U64P, U64P, P, P]
     lib.oracle_fff.restype = ctypes.c_int
+    lib.oracle_fff_owners.argtypes = [P, P, ctypes.c_int32, ctypes.c_int, P, ctypes.c_int32, ctypes.c_int, P]
+    lib.oracle_fff_owners.restype = ctypes.c_int
     lib.oracle_owner_coloured.argtypes = [P, P, ctypes.c_int32, ctypes.c_int, P, U64P, U64P]
     lib.oracle_owner_coloured.restype = ctypes.c_int
     lib.oracle_scale_estimate.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int]
@@ -155,6 +157,19 @@ def count(g, k: int, per_owner: bool = False, per_vertex: bool = False,
     """Exact FFF_k: returns (q_k, per_owner or None, per_vertex or None).
     u_range=(lo, hi) restricts the owners u to original ids lo..hi-1."""
     return _fff(g, k, 0, 0, per_owner, per_vertex, u_range, nthreads)
+
+
+def count_owners(g, k: int, owners, nthreads: int = 0) -> np.ndarray:
+    """Exact per-owner counts q_{u,k-1} for an explicit list of owners (the
+    same Reduce 3 routine as count(), one owner per thread): out[i] is the
+    count of owners[i]."""
+    off, adj = _csr(g)
+    own = np.ascontiguousarray(owners, dtype=np.int32)
+    out = np.zeros(max(own.size, 1), dtype=np.uint64)
+    _check(_load().oracle_fff_owners(off.ctypes.data, adj.ctypes.data, g.n, k,
+                                     own.ctypes.data if own.size else None, int(own.size), nthreads,
+                                     out.ctypes.data))
+    return out[: own.size]
 
 
 def estimate(g, k: int, colours: int, seed: int, per_owner: bool = False,

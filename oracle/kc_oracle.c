@@ -394,6 +394,41 @@ int oracle_fff(const int64_t* off, const int32_t* adj, int32_t n, int k,
     return fff_run(off, adj, n, k, &sm, u_lo, u_hi, nthreads, total_lo, total_hi, per_owner, per_vertex);
 }
 
+/* Exact FFF_k Reduce 3 counts q_{u,k-1} of an explicit list of owners (Sec. 3:
+ * each clique is counted by its smallest vertex), one owner per OpenMP task:
+ * out[i] = q_{owners[i],k-1}.  The same per-owner routine as oracle_fff; this
+ * only lets a test check scattered owners of a large graph without running
+ * every owner in between. */
+int oracle_fff_owners(const int64_t* off, const int32_t* adj, int32_t n, int k,
+                      const int32_t* owners, int32_t nowners, int nthreads, uint64_t* out)
+{
+    if (n < 0 || k < 1 || nowners < 0 || (nowners > 0 && (!owners || !out))) return OR_EINVAL;
+    for (int32_t i = 0; i < nowners; ++i)
+        if (owners[i] < 0 || owners[i] >= n) return OR_EINVAL;
+    int st = OR_OK;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1)
+#else
+    (void)nthreads;
+#endif
+    for (int32_t i = 0; i < nowners; ++i) {
+        u128 q = 0;
+        int s = OR_OK;
+        if (k == 1) q = 1;
+        else s = owner_work(off, adj, owners[i], k, &(sampler){ 0, 0, NULL, 0, 0, NULL }, NULL, &q);
+        if (s == OR_OK && (q >> 64)) s = OR_OVERFLOW;
+        if (s != OR_OK) {
+#ifdef _OPENMP
+#pragma omp critical
+#endif
+            { if (st == OR_OK) st = s; }
+        }
+        out[i] = (uint64_t)q;
+    }
+    return st;
+}
+
 /* Plain pair sampling (Sec. 6) over owners u in [u_lo, u_hi): the sampled
  * count S (before scaling) and per-owner sampled counts; p in (0, 1], p = 1
  * emits every pair. */

@@ -431,3 +431,20 @@ def test_listing_complete_graph():
         L = oracle.list_cliques(g, k)
         assert len(L) == comb(12, k)
         assert len({tuple(sorted(r)) for r in L.tolist()}) == comb(12, k)
+
+
+def test_count_owners_matches_per_owner_and_closed_form():
+    """oracle.count_owners (explicit owner lists) agrees with the per-owner
+    output of the full count, and with K_n's closed form: the vertex of rank
+    r owns C(n-1-r, k-1) k-cliques (Sec. 3: each clique counted by its
+    smallest vertex)."""
+    g = kcgen.chung_lu(3000, 20000, 2.1, 300.0, 2)
+    rng = np.random.default_rng(1)
+    for k in (1, 2, 3, 4, 5):
+        _, po, _ = oracle.count(g, k, per_owner=True)
+        own = rng.choice(g.n, 300, replace=False)
+        assert np.array_equal(oracle.count_owners(g, k, own), po[own]), k
+    kn = kcgen.complete(20)
+    for k in (3, 6):
+        got = oracle.count_owners(kn, k, np.arange(20))
+        assert [int(x) for x in got] == [comb(19 - r, k - 1) for r in range(20)]
