@@ -35,11 +35,14 @@ UNIT = "k-cliques/s"
 WORKLOAD = "chung_lu n=1e6 m~2e7 gamma=2.1 wmax=20000 seed=1+rank, exact k=3..6, per-vertex+per-owner"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "roofline_traffic.json")
-# Word-operation peak of the counting kernels: one 32-bit AND, population
-# count and add per word; the population count issues at 16 lanes per clock
-# per SM, so the peak is 16 x 152 SMs x clock (derivation in the design doc).
+# Word-operation peak of the counting kernels.  A word-op is one 32-bit AND
+# of a candidate-set word with a bitmap row word, its population count, and
+# the add of that count.  AND and add issue on the integer ALUs at 128 lanes
+# per SM per clock; the population count runs on the narrower unit that
+# serves POPC/FLO/BREV, at 16 lanes per SM per clock.  That unit is the
+# narrowest one every word-op needs, so the peak is 16 x SMs x SM clock
+# (the maximum SM clock of the measured peaks file).
 POPC_LANES_PER_SM_CLK = 16
-NUM_SMS = 152
 
 
 def parse():
@@ -427,7 +430,8 @@ def main():
     kmax_ms = statistics.mean(k_ms[kmax])
     pk, pk_kind = peaks()
     clock_mhz = float(pk.get("sm_max_mhz", 2070.0))
-    peak_wops = POPC_LANES_PER_SM_CLK * NUM_SMS * clock_mhz * 1e6 / 1e12  # Tword-op/s
+    num_sms = torch.cuda.get_device_properties(local).multi_processor_count
+    peak_wops = POPC_LANES_PER_SM_CLK * num_sms * clock_mhz * 1e6 / 1e12  # Tword-op/s
     achieved = work / (kmax_ms * 1e-3) / 1e12
     traffic = None
     try:

@@ -90,20 +90,28 @@ kc_status kc_build_csr(int32_t n, const int32_t* src, const int32_t* dst, int64_
  * Gamma+(u) = {x in Gamma(u) : u < x}.  The result is kept resident as an
  * oriented CSR in rank space (vertex r is the r-th smallest in the order;
  * row r lists the ranks of Gamma+(r) ascending, i.e. in the order), plus the
- * work queue used by the counting kernels (owners by |Gamma+| descending).
+ * work queue used by the counting kernels (see kc_export).
  *   off, adj  the canonical CSR (arrays; host or, with KC_DEVICE_PTRS, device)
  *   n, m      vertices and undirected edges (adj has 2m entries); n >= 0
  *   flags     KC_DEVICE_PTRS, KC_VALIDATE (symmetry, sorted rows, no loops,
  *             no repeats; failures return KC_EINVAL)
  *   out       receives the new graph handle (NULL on failure)
- * Synchronous: returns when the oriented graph is complete on `stream`.
+ * Asynchronous on `stream` (without KC_VALIDATE): host inputs are copied
+ * before the call returns; device inputs must stay unchanged until the
+ * orientation has run on `stream`.  The handle can be passed on at once: the
+ * first later call that needs the orientation's results on the host (any
+ * count, estimate, listing, kc_info, kc_export, kc_footprint) waits for it,
+ * and reports a failure of the orientation itself there (KC_ETIMEOUT, or
+ * KC_EINVAL for a CSR that is not symmetric and simple).  Device memory comes
+ * from a pool owned by the library, which keeps freed blocks for reuse.
  * Errors: KC_EINVAL, KC_ENOMEM, KC_ECUDA.
  */
 kc_status kc_orient(const int64_t* off, const int32_t* adj, int32_t n, int64_t m,
                     unsigned flags, void* stream, kc_graph** out);
 
-/* Release a graph and its device memory.  NULL is ignored.  The caller must
- * ensure no call using `g` is still running on any stream. */
+/* Release a graph and its device memory (back to the library's pool).  NULL
+ * is ignored.  Waits for the graph's orientation if it is still running; the
+ * caller must ensure no other call using `g` is still running on any stream. */
 void kc_free(kc_graph* g);
 
 typedef struct {
@@ -123,7 +131,16 @@ kc_status kc_info(const kc_graph* g, kc_graph_info* info);
  *   perm     array of n: perm[r] = vertex with rank r
  *   off_plus array of n+1: row offsets of the oriented CSR (rank space)
  *   adj_plus array of m: ranks of Gamma+ of each row, ascending
- *   queue    array of n: owners (ranks) by |Gamma+| descending, ties by rank
+ *   queue    array of n: the owners (ranks) in the order the counting
+ *            kernels take them.  Owners are grouped by the width of their
+ *            bitmap row: |Gamma+| > 1024 first, then 513..1024, 257..512,
+ *            129..256, 65..128, 33..64, 1..32, and 0 last.  In the 1..32
+ *            group they go by |Gamma+| descending (so the Reduce 1 filter
+ *            |Gamma+| >= k-1 keeps a prefix of the queue); in the wider groups
+ *            by the work estimate w(u) = sum over x in Gamma+(u) of
+ *            |Gamma+(x)|, descending, compared after quantisation to
+ *            q(w) = min(31, max(0, 2 b + f - 20)), b = floor(log2(w + 1))
+ *            and f the bit of w + 1 below its leading one; ties by rank.
  * Any array may be NULL.  Errors: KC_EINVAL, KC_ECUDA.
  */
 kc_status kc_export(const kc_graph* g, unsigned flags, int32_t* rank, int32_t* perm,
@@ -271,7 +288,8 @@ kc_status kc_count_batch(const kc_graph* const* gs, int ng, int k, unsigned flag
  * Tuning knobs (process-wide; they change speed, never results).
  *   KC_PARAM_SMEM_MAX_WORDS  owners whose bitmap rows need at most this many
  *       32-bit words (|Gamma+(u)| <= 32 * value) keep G+(u) in shared memory;
- *       wider owners use global-memory tiles.  1..32, default 32.
+ *       wider owners use global-memory tiles.  1, 2, 4, 8, 16 or 32 (the
+ *       queue's group widths), default 32.
  *   KC_PARAM_LAUNCH_COUNT  read: kernels launched by this process so far;
  *       write 0 to reset.
  *   KC_PARAM_WORK_COUNT  write 1 (0) to turn on (off) work counting in the

@@ -235,19 +235,19 @@ void kc_free(kc_graph* g)
 {
     if (!g) return;
     kc::DeviceGuard dg(g->device);
-    cudaFree(g->rank);
-    cudaFree(g->perm);
-    cudaFree(g->deg);
-    cudaFree(g->dplus);
-    cudaFree(g->offp);
-    cudaFree(g->adjp);
-    cudaFree(g->queue);
+    if (g->done) {
+        cudaEventSynchronize(g->done);  // the orientation may still be running
+        cudaEventDestroy(g->done);
+    }
+    kc::pool_free(g->block, 0);
+    kc::stats_slot_put(g->hstats);
     delete g;
 }
 
 kc_status kc_info(const kc_graph* g, kc_graph_info* info)
 {
     if (!g || !info) return KC_EINVAL;
+    KC_TRY(kc::ready(g));
     info->n = g->n;
     info->m = g->m;
     info->max_dplus = g->max_dplus;
@@ -261,6 +261,7 @@ kc_status kc_export(const kc_graph* g, unsigned flags, int32_t* rank, int32_t* p
 {
     if (!g) return KC_EINVAL;
     kc::DeviceGuard dg(g->device);
+    KC_TRY(kc::ready(g));
     cudaStream_t s = (cudaStream_t)stream;
     const cudaMemcpyKind kind = (flags & KC_DEVICE_PTRS) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     const size_t n = (size_t)g->n;
@@ -278,6 +279,7 @@ kc_status kc_count(const kc_graph* g, int k, unsigned flags, uint64_t* total, ui
 {
     if (!g || !total || k < 1 || k > KC_MAX_K) return KC_EINVAL;
     kc::DeviceGuard dg(g->device);
+    KC_TRY(kc::ready(g));
     return kc::run_count(g, k, 0, 0, flags, total, per_vertex, per_owner, (cudaStream_t)stream);
 }
 
@@ -286,6 +288,7 @@ kc_status kc_estimate(const kc_graph* g, int k, uint32_t colours, uint64_t seed,
 {
     if (!g || !sampled || k < 1 || k > KC_MAX_K || colours < 1) return KC_EINVAL;
     kc::DeviceGuard dg(g->device);
+    KC_TRY(kc::ready(g));
     kc_status st = kc::run_count(g, k, colours, seed, flags, sampled, nullptr, per_owner, (cudaStream_t)stream);
     if (st != KC_OK) return st;
     if (estimate && !(flags & KC_DEVICE_PTRS)) {
@@ -301,6 +304,7 @@ kc_status kc_estimate_pairs(const kc_graph* g, int k, double p, uint64_t seed, u
 {
     if (!g || !sampled || k < 1 || k > KC_MAX_K || !(p > 0.0 && p <= 1.0)) return KC_EINVAL;
     kc::DeviceGuard dg(g->device);
+    KC_TRY(kc::ready(g));
     // p = 1 keeps every pair: the exact count
     const bool pair = p < 1.0;
     const uint64_t thr = pair ? (uint64_t)std::ldexp(p, 64) : 0;
@@ -320,6 +324,7 @@ kc_status kc_list(const kc_graph* g, int k, unsigned flags, int32_t* buf, int64_
 {
     if (!g || !buf || !fn || !listed || k < 1 || k > KC_MAX_K || cap < 1) return KC_EINVAL;
     kc::DeviceGuard dg(g->device);
+    KC_TRY(kc::ready(g));
     return kc::list_run(g, k, flags, buf, cap, fn, user, listed, (cudaStream_t)stream);
 }
 
@@ -327,6 +332,7 @@ kc_status kc_footprint(const kc_graph* g, int k, int per_vertex, int per_owner, 
                        uint64_t* bytes)
 {
     if (!g || !bytes || k < 1 || k > KC_MAX_K) return KC_EINVAL;
+    KC_TRY(kc::ready(g));
     const uint64_t n = (uint64_t)(g->n > 0 ? g->n : 1);
     uint64_t b = 256;  // total, cursors, work counter
     const uint64_t arrays = (per_vertex ? 1 : 0) + (per_owner ? 1 : 0);
@@ -345,6 +351,7 @@ kc_status kc_count_part(const kc_graph* g, int k, int part, int nparts, unsigned
 {
     if (!g || !total || k < 3 || k > KC_MAX_K || nparts < 1 || part < 0 || part >= nparts) return KC_EINVAL;
     kc::DeviceGuard dg(g->device);
+    KC_TRY(kc::ready(g));
     return kc::run_count(g, k, 0, 0, flags, total, per_vertex, per_owner, (cudaStream_t)stream, part, nparts);
 }
 
@@ -355,6 +362,7 @@ kc_status kc_count_batch(const kc_graph* const* gs, int ng, int k, unsigned flag
     for (int i = 0; i < ng; ++i)
         if (!gs[i] || gs[i]->device != gs[0]->device) return KC_EINVAL;
     kc::DeviceGuard dg(gs[0]->device);
+    for (int i = 0; i < ng; ++i) KC_TRY(kc::ready(gs[i]));
     cudaStream_t s = (cudaStream_t)stream;
     const bool dev = (flags & KC_DEVICE_PTRS) != 0;
     if (k <= 2) {

@@ -56,7 +56,9 @@ kc_status dfs_reg_launch(const cc::Ctx& c, int W, bool pv, bool col, cudaStream_
 
 kc_status set_smem_max_words(int64_t v)
 {
-    if (v < 1 || v > kClassWords[kNumSmemClasses - 1]) return KC_EINVAL;
+    // a class width: the queue is grouped by these classes, so every
+    // shared-memory / global-tile split falls on a class boundary
+    if (v < 1 || v > kClassWords[kNumSmemClasses - 1] || (v & (v - 1)) != 0) return KC_EINVAL;
     g_smem_max_words = (int)v;
     return KC_OK;
 }
@@ -526,10 +528,7 @@ int slot_words(int slot)
 
 void class_range(const kc_graph* g, int k, int slot, int64_t* q0, int64_t* q1)
 {
-    auto ge_at = [&](int64_t t) -> int64_t {
-        if (t <= 0) return g->n;
-        return t <= (int64_t)g->max_dplus ? g->ge[(size_t)t] : 0;
-    };
+    auto ge_at = [&](int64_t t) -> int64_t { return kc::ge_at(g, t); };
     const int64_t dmin = k - 1;  // Reduce 1 filter
     const int maxw = smem_max_words();
     *q0 = *q1 = 0;

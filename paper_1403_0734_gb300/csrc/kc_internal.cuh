@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cstdint>
 #include <cstddef>
+#include <mutex>
 #include <vector>
 #include <cuda_runtime.h>
 
@@ -56,6 +57,18 @@ constexpr int kOwnerSlots = 7;
 
 // ---------------------------------------------------------- graph handle
 
+// Statistics of an orientation, written by the orientation kernels and
+// copied to (pinned) host memory at the end of kc_orient.
+struct OrientStats {
+    unsigned long long wedges;       // sum over u of C(d+(u), 2)
+    unsigned long long eq[33];       // #{u : d+(u) == t}, t = 0..32
+    unsigned long long cls[6];       // #{u : d+(u) in (32*2^i, 64*2^i]}, i = 0..4; cls[5]: d+ > 1024
+    unsigned int max_dplus;
+    unsigned int max_deg;
+    int err_timeout;                 // a bounded device-side wait gave up
+    int err_input;                   // sum of d+ != m: the CSR was not symmetric and simple
+};
+
 }  // namespace kc
 
 struct kc_graph {
@@ -70,31 +83,20 @@ struct kc_graph {
     int32_t* dplus = nullptr;  // [n]  |Gamma+|, rank space
     int64_t* offp = nullptr;   // [n+1] oriented CSR offsets, rank space
     int32_t* adjp = nullptr;   // [m]  oriented CSR columns (ranks), rows ascending
-    int32_t* queue = nullptr;  // [n]  ranks by d+ descending, ties by rank
-    std::vector<int64_t> ge;   // host: ge[t] = #{u : d+(u) >= t}, t = 0..max_dplus+1
+    int32_t* queue = nullptr;  // [n]  owners (ranks): bitmap class, then work estimate (see kc.h)
+    void* block = nullptr;     // one pool allocation holding the arrays above
     int64_t bytes = 0;
+    // host statistics: valid once ready() has returned KC_OK
+    kc::OrientStats* hstats = nullptr;  // pinned slot the orientation copies its statistics into
+    cudaEvent_t done = nullptr;         // recorded after the last orientation kernel
+    mutable std::mutex mu;
+    mutable bool is_ready = false;
+    mutable kc_status ready_status = KC_OK;
+    int64_t ge_small[34] = {};          // #{u : d+(u) >= t}, t = 0..33
+    int64_t ge_cls[7] = {};             // #{u : d+(u) >= 32*2^i + 1}, i = 0..5; [6] = 0
 };
 
 namespace kc {
-
-// ------------------------------------------------------------ primitives
-
-// Exclusive scan of int32 values into int64 offsets: out[0] = 0,
-// out[i+1] = out[i] + in[i]; out has n+1 entries.  `tmp` must hold
-// scan_tmp_elems(n) int64 values.
-size_t scan_tmp_elems(int64_t n);
-kc_status scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, int64_t* tmp,
-                          cudaStream_t s);
-
-// Stable LSD radix sort of (key, value) pairs by the low `bits` bits of the
-// 32-bit keys.  Buffers are ping-ponged; the sorted result is returned in
-// (*keys, *vals) which point to either the input or the alternate buffers.
-// `hist` must hold radix_hist_elems(n) int32 values, `tmp` scan_tmp_elems of
-// that many values.
-int64_t radix_hist_elems(int64_t n);
-kc_status radix_sort_pairs(uint32_t** keys, int32_t** vals, uint32_t* keys_alt,
-                           int32_t* vals_alt, int64_t n, int bits, int32_t* hist,
-                           int64_t* hist_scan, int64_t* tmp, cudaStream_t s);
 
 // ------------------------------------------------------------ counting
 
@@ -146,6 +148,27 @@ kc_status list_run(const kc_graph* g, int k, unsigned flags, int32_t* buf, int64
 int tri_enabled();
 kc_status set_tri(int64_t v);
 
+// Stream-ordered allocation from the library's memory pool of the current
+// device (a cudaMemPool that keeps freed memory for reuse instead of
+// returning it at every synchronisation, so repeated calls do not pay for
+// cudaMalloc).  Free with pool_free on a stream ordered after the last use.
+kc_status pool_alloc(void** p, size_t bytes, cudaStream_t s);
+void pool_free(void* p, cudaStream_t s);
+
+// Pinned host slot for one graph's OrientStats (process-wide free list).
+OrientStats* stats_slot_get();
+void stats_slot_put(OrientStats* p);
+
+// Waits (once per graph) for the orientation to finish and fills the host
+// statistics; returns the orientation's status (KC_ETIMEOUT, KC_EINVAL for a
+// CSR that was not symmetric and simple, KC_ECUDA).  Every entry point that
+// reads g's host statistics or runs on another stream calls it first.
+kc_status ready(const kc_graph* g);
+
+// #{u : d+(u) >= t}; t must be <= 33 or one of 65, 129, 257, 513, 1025
+// (the boundaries of the bitmap classes).
+int64_t ge_at(const kc_graph* g, int64_t t);
+
 // Stream-ordered scratch, released on scope exit (after the stream's work).
 struct Scratch {
     cudaStream_t s;
@@ -153,17 +176,13 @@ struct Scratch {
     explicit Scratch(cudaStream_t st) : s(st) {}
     ~Scratch()
     {
-        for (void* p : ptrs) cudaFreeAsync(p, s);
+        for (void* p : ptrs) pool_free(p, s);
     }
     template <typename T>
     kc_status get(T** p, int64_t count)
     {
         void* q = nullptr;
-        cudaError_t e = cudaMallocAsync(&q, (size_t)std::max<int64_t>(count, 1) * sizeof(T), s);
-        if (e != cudaSuccess) {
-            set_cuda_error(e, "cudaMallocAsync");
-            return e == cudaErrorMemoryAllocation ? KC_ENOMEM : KC_ECUDA;
-        }
+        KC_TRY(pool_alloc(&q, (size_t)std::max<int64_t>(count, 1) * sizeof(T), s));
         ptrs.push_back(q);
         *p = (T*)q;
         return KC_OK;

@@ -310,9 +310,9 @@ kc_status list_run(const kc_graph* g, int k, unsigned flags, int32_t* buf, int64
         KC_CK(cudaMemcpyAsync(dp.data(), g->dplus, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
         KC_CK(cudaStreamSynchronize(s));
         for (int32_t r = 0; r < n; ++r) cnt[r] = (unsigned long long)dp[r];
-        qend = g->max_dplus >= 1 ? g->ge[1] : 0;
+        qend = ge_at(g, 1);
     } else {
-        qend = g->max_dplus >= k - 1 ? g->ge[(size_t)(k - 1)] : 0;
+        qend = ge_at(g, k - 1);
         unsigned long long* po = nullptr;
         KC_TRY(sc.get(&po, n));
         KC_CK(cudaMemsetAsync(po, 0, (size_t)n * sizeof(unsigned long long), s));

@@ -76,6 +76,7 @@ extern "C" kc_status kc_count_static(const kc_graph* g, int k, unsigned flags, u
         int prev, dev;
         ~Restore() { if (prev >= 0 && prev != dev) cudaSetDevice(prev); }
     } restore{prev, g->device};
+    KC_TRY(kc::ready(g));
 
     if (k <= 2) {  // q_1 = n, q_2 = m: no kernel and no scratch
         static thread_local unsigned long long tv[2];

@@ -77,7 +77,7 @@ def test_params(lib):
     kc.set_param(kc.KC_PARAM_SMEM_MAX_WORDS, 4)
     assert kc.get_param(kc.KC_PARAM_SMEM_MAX_WORDS) == 4
     kc.set_param(kc.KC_PARAM_SMEM_MAX_WORDS, 32)
-    for bad in (0, 33):
+    for bad in (0, 3, 12, 33, 64):  # the queue's group widths only: powers of two up to 32
         with pytest.raises(kc.KcError):
             kc.set_param(kc.KC_PARAM_SMEM_MAX_WORDS, bad)
     with pytest.raises(kc.KcError):

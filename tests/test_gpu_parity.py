@@ -59,6 +59,36 @@ def graph(name):
     return _cache[name]
 
 
+def quantise_work(w):
+    """q(w) = min(31, max(0, 2 b + f - 20)): b = floor(log2(w + 1)), f = the
+    bit of w + 1 below its leading one (the queue's work-estimate order, kc.h)."""
+    x = int(w) + 1
+    b = x.bit_length() - 1
+    f = (x >> (b - 1)) & 1 if b >= 1 else 0
+    return min(31, max(0, 2 * b + f - 20))
+
+
+def expected_queue(offp, adjp):
+    """The documented owner queue from an oriented CSR: groups by bitmap
+    width (|Gamma+| > 1024 first ... 1..32, then 0), |Gamma+| descending in
+    the 1..32 group, quantised work estimate sum |Gamma+(x)| descending in
+    the wider groups, ties by rank."""
+    dplus = np.diff(offp)
+    n = dplus.size
+    key = np.zeros(n, dtype=np.int64)
+    for r in range(n):
+        d = int(dplus[r])
+        if d == 0:
+            key[r] = 7 << 5
+        elif d <= 32:
+            key[r] = (6 << 5) | (32 - d)
+        else:
+            cls = 5 if d <= 64 else 4 if d <= 128 else 3 if d <= 256 else 2 if d <= 512 else 1 if d <= 1024 else 0
+            w = int(dplus[adjp[offp[r]:offp[r + 1]]].sum())
+            key[r] = (cls << 5) | (31 - quantise_work(w))
+    return np.lexsort((np.arange(n), key))
+
+
 def check_count(kc, g, G, k):
     total, pv, po = kc.count(G, k, per_vertex=True, per_owner=True)
     ot, opo, opv = oracle.count(g, k, per_owner=True, per_vertex=True)
@@ -83,8 +113,7 @@ def test_orientation_matches_oracle(kc, name):
     assert np.array_equal(ex["off_plus"], offp)
     assert np.array_equal(ex["adj_plus"], adjp)
     dplus = np.diff(offp)
-    exp_queue = np.lexsort((np.arange(g.n), -dplus))
-    assert np.array_equal(ex["queue"], exp_queue)
+    assert np.array_equal(ex["queue"], expected_queue(offp, adjp))
     assert G.max_dplus == int(dplus.max())
     assert G.wedges == int((dplus * (dplus - 1) // 2).sum())
     assert G.m == g.m
@@ -99,6 +128,47 @@ def test_orientation_long_rows(kc):
     assert np.array_equal(ex["perm"], np.arange(300))
     for r in (0, 1, 150, 298, 299):
         assert np.array_equal(ex["adj_plus"][ex["off_plus"][r]:ex["off_plus"][r + 1]], np.arange(r + 1, 300))
+
+
+def test_orientation_cta_rows(kc):
+    """Rows longer than a warp handles (one CTA per row, kept entries sorted
+    in shared memory): K_1100 whose vertex v also carries pi(v) pendant
+    leaves, pi a seeded permutation, so the order of the core follows pi and
+    not the ids; each core row's Gamma+ is the core vertices of larger pi."""
+    n = 1100
+    pi = np.random.default_rng(5).permutation(n)
+    iu, ju = np.triu_indices(n, 1)
+    leaves_of = np.repeat(np.arange(n), pi)
+    leaf_ids = n + np.arange(leaves_of.size)
+    e = np.concatenate([np.stack([iu, ju], 1), np.stack([leaves_of, leaf_ids], 1)])
+    g = kcgen.from_edges(n + leaves_of.size, e)
+    G = kc.orient(g.off, g.adj, validate=True)
+    ex = kc.export(G)
+    rank = ex["rank"]
+    for v in range(0, n, 37):
+        want = np.sort(rank[np.flatnonzero(pi > pi[v])])
+        r = rank[v]
+        assert np.array_equal(ex["adj_plus"][ex["off_plus"][r]:ex["off_plus"][r + 1]], want), v
+    assert np.array_equal(np.argsort(rank[:n]), np.argsort(pi))  # the core ordered by degree = n - 1 + pi
+    assert G.max_dplus == n - 1
+
+
+def test_orientation_global_sort_rows(kc):
+    """A row with more than 8192 kept entries (sorted in place in global
+    memory): K_8300 built directly as a CSR; equal degrees, so the order is
+    the id order and row r of the oriented CSR is r+1..n-1."""
+    n = 8300
+    off = np.arange(n + 1, dtype=np.int64) * (n - 1)
+    full = np.tile(np.arange(n, dtype=np.int32), n).reshape(n, n)
+    adj = full[~np.eye(n, dtype=bool)].astype(np.int32)
+    del full
+    G = kc.orient(off, adj)
+    ex = kc.export(G)
+    assert np.array_equal(ex["perm"], np.arange(n))
+    for r in (0, 1, 2, 100, 4000, 8298, 8299):
+        assert np.array_equal(ex["adj_plus"][ex["off_plus"][r]:ex["off_plus"][r + 1]], np.arange(r + 1, n)), r
+    assert G.max_dplus == n - 1 and G.m == n * (n - 1) // 2
+    G.free()
 
 
 # ------------------------------------------------------------ exact counts
