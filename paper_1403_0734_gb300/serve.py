@@ -22,6 +22,16 @@ from dataclasses import dataclass, field
 import numpy as np
 
 
+class RequestError(RuntimeError):
+    """A request's backend call failed; `results` holds every request's
+    Result (failed ones with their error)."""
+
+    def __init__(self, rid: int, error: str, results):
+        super().__init__(f"request {rid} failed: {error}")
+        self.rid = rid
+        self.results = results
+
+
 @dataclass
 class Request:
     rid: int
@@ -40,6 +50,7 @@ class Result:
     arrival: float
     start: float
     end: float
+    error: str | None = None  # the backend's exception, if the request failed
 
     @property
     def latency(self) -> float:
@@ -118,18 +129,27 @@ class Server:
                         return
                     self._cv.wait()
             start = self._now()
-            value, est = self._backend(req, stream)
-            end = self._now()
-            with self._cv:
-                self._in_use -= fp
-                self._running -= 1
-                self._results.append(Result(req.rid, int(value), float(est), req.arrival, start, end))
-                self._done += 1
-                self._cv.notify_all()
+            value, est, err = 0, float("nan"), None
+            try:
+                value, est = self._backend(req, stream)
+            except Exception as e:  # recorded per request; run() raises after the rest finish
+                err = f"{type(e).__name__}: {e}"
+            finally:
+                end = self._now()
+                with self._cv:  # the slot, its footprint and the request are always released
+                    self._in_use -= fp
+                    self._running -= 1
+                    self._results.append(Result(req.rid, int(value), float(est), req.arrival, start, end, err))
+                    self._done += 1
+                    self._cv.notify_all()
 
-    def run(self, requests, stream_factory=None, realtime: bool = True):
+    def run(self, requests, stream_factory=None, realtime: bool = True, raise_errors: bool = True):
         """Serve `requests` (arrival times relative to the start); returns the
-        results ordered by request id and the makespan in seconds."""
+        results ordered by request id and the makespan in seconds.  A request
+        whose backend call raised still completes (its Result carries the
+        error) and does not hold up the others; with raise_errors, run()
+        raises RequestError for the first failed request once every request
+        has finished."""
         reqs = sorted(requests, key=lambda r: r.arrival)
         fps = [self._footprint(r) for r in reqs]
         if self.budget is not None and any(fp > self.budget for fp in fps):
@@ -156,7 +176,11 @@ class Server:
         makespan = self._now()
         for w in workers:
             w.join()
-        return sorted(self._results, key=lambda x: x.rid), makespan
+        results = sorted(self._results, key=lambda x: x.rid)
+        failed = [r for r in results if r.error is not None]
+        if raise_errors and failed:
+            raise RequestError(failed[0].rid, failed[0].error, results)
+        return results, makespan
 
 
 def latency_stats(results):

@@ -77,3 +77,45 @@ def test_oversized_request_rejected(graphs):
     srv = serve.Server(graphs, slots=2, budget_bytes=10, backend=lambda r, s: (0, 0.0), footprint=lambda r: 11)
     with pytest.raises(ValueError):
         srv.run(serve.poisson_stream(2, 10.0, len(graphs), 1))
+
+
+def test_failing_request_does_not_hang_the_server(graphs):
+    """A backend that raises (e.g. an allocation failure in the library) for
+    some requests: every request still completes, the slots and footprint are
+    released, the failure is reported per request and run() raises after the
+    others have finished."""
+    tracker = {"running": 0, "peak": 0}
+    ok = make_backend(graphs, 0.002, tracker)
+
+    def backend(req, stream):
+        if req.rid % 5 == 3:
+            raise MemoryError("device allocation failed")
+        return ok(req, stream)
+
+    reqs = serve.poisson_stream(40, 0.0, len(graphs), seed=3, kmin=3, kmax=4)
+    srv = serve.Server(graphs, slots=3, budget_bytes=100, backend=backend, footprint=lambda r: 40)
+    done = {}
+
+    def run():
+        try:
+            srv.run(reqs, realtime=False)
+        except serve.RequestError as e:
+            done["err"] = e
+
+    t = threading.Thread(target=run, daemon=True)
+    t.start()
+    t.join(timeout=60)
+    assert not t.is_alive(), "server hung after a failed request"
+    err = done["err"]
+    assert err.rid == 3 and "MemoryError" in str(err)
+    res = err.results
+    assert len(res) == len(reqs) and srv._in_use == 0 and srv._running == 0
+    for r, q in zip(res, sorted(reqs, key=lambda x: x.rid)):
+        if q.rid % 5 == 3:
+            assert r.error is not None
+        else:
+            assert r.error is None and r.value == expected(graphs, q)
+    # the same server runs a clean stream afterwards
+    res2, _ = serve.Server(graphs, slots=3, backend=ok).run(
+        serve.poisson_stream(10, 0.0, len(graphs), seed=4, kmin=3, kmax=4), realtime=False)
+    assert all(r.error is None for r in res2)
