@@ -116,6 +116,6 @@ def test_failing_request_does_not_hang_the_server(graphs):
         else:
             assert r.error is None and r.value == expected(graphs, q)
     # the same server runs a clean stream afterwards
-    res2, _ = serve.Server(graphs, slots=3, backend=ok).run(
+    res2, _ = serve.Server(graphs, slots=3, backend=ok, footprint=lambda r: 1).run(
         serve.poisson_stream(10, 0.0, len(graphs), seed=4, kmin=3, kmax=4), realtime=False)
     assert all(r.error is None for r in res2)
