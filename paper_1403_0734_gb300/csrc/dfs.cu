@@ -197,27 +197,32 @@ __device__ __forceinline__ uint32_t leaf2_rep(uint32_t C, int Wd, const uint32_t
         }
         const uint32_t cw = __shfl_sync(kFull, C, w);
         const uint32_t ex = __shfl_sync(kFull, excl, w);
+        unsigned words = 0;
         if (j < total) {
             const int e = w * 32 + (int)__fns(cw, 0, (int)(j - ex) + 1);
             uint32_t f = 0;
             if (WM >= 4) {
+                // upper rows (no memberships) hold nothing below e's group
+                const int elo = PV ? glo : max(glo, e >> 7);
                 const uint4* A4 = (const uint4*)(A + (int64_t)e * RS);
 #pragma unroll
                 for (int q = 0; q < WM / 4; ++q) {
-                    if (q < glo || q > ghi) continue;
+                    if (q < elo || q > ghi) continue;
                     const uint4 a = A4[q];
                     f += (uint32_t)(__popc(Cr[4 * q] & a.x) + __popc(Cr[4 * q + 1] & a.y) +
                                     __popc(Cr[4 * q + 2] & a.z) + __popc(Cr[4 * q + 3] & a.w));
                 }
+                words = (unsigned)(4 * (ghi - elo + 1));
             } else {
                 const uint32_t* Ae = A + (int64_t)e * RS;
 #pragma unroll
                 for (int q = 0; q < WM; ++q) f += (uint32_t)__popc(Cr[q] & Ae[q]);
+                words = (unsigned)WM;
             }
             S += f;
             if (PV && f) pv_add(pvlo, pvhi, e, f);
         }
-        if (wk) *wk += (unsigned long long)__reduce_add_sync(kFull, j < total ? (unsigned)Wd : 0u);
+        if (wk) *wk += (unsigned long long)__reduce_add_sync(kFull, words);
     }
     const uint32_t E = __reduce_add_sync(kFull, S);
     return PV ? E / 2u : E;
@@ -233,15 +238,18 @@ __device__ __forceinline__ uint32_t leaf2_any(uint32_t C, int w0, int Wd, const 
 }
 
 // All children of a node whose candidate set C (lane w holds word w) still
-// needs three vertices: the cliques below are the triangles of G[C].
-// Without memberships each lane takes one child e of C, forms Ce = C & N(e)
-// above e in its own registers and counts the edges inside Ce by walking
-// Ce's elements itself (128-bit row loads, no shuffles).  With memberships
-// (symmetric rows) each lane takes one element f of C instead and counts the
-// edges inside N(f) & C -- the triangles of G[C] through f, f's membership
-// increment -- so no lane writes another lane's counter; the number of
-// triangles is a third of their sum.  sC: per-warp buffer of WM words
-// (16-byte aligned).
+// needs three vertices: the cliques below are the triangles of G[C].  Each
+// lane takes one element e of C and forms Ce = C & N(e) in its own
+// registers: without memberships N(e) is e's upper row (the elements above
+// e), and the lane counts the edges inside Ce -- the triangles whose smallest
+// vertex is e; with memberships (symmetric rows) N(e) is e's whole row and
+// the lane counts the edges inside it -- the triangles of G[C] through e,
+// e's membership increment (so no lane writes another lane's counter); the
+// number of triangles is a third of their sum.  The edges inside Ce are
+// counted as the sum over f in Ce of popc(Ce & up(f)), where up(f) is f's
+// row above f: only the words from f's own word on are read (with symmetric
+// rows the lower part is masked off).  sC: per-warp buffer of WM words
+// (16-byte aligned).  The work counter gets the words actually ANDed.
 template <bool PV, int WM>
 __device__ unsigned long long penult3(uint32_t C, int Wd, const uint32_t* A, int RS, uint32_t* pvlo,
                                       uint32_t* pvhi, uint32_t* sC, int lane, unsigned long long* wk)
@@ -253,6 +261,7 @@ __device__ unsigned long long penult3(uint32_t C, int Wd, const uint32_t* A, int
     const uint32_t nz = __ballot_sync(kFull, lane < WM && C != 0u);
     if (nz == 0u) return 0ull;
     const int glo = (__ffs(nz) - 1) >> 2, ghi = (31 - __clz(nz)) >> 2;
+    const int xhi = 4 * ghi + 3;  // last word that can be non-zero
     const uint32_t pc = (uint32_t)__popc(C);
     uint32_t pre = pc;
 #pragma unroll
@@ -275,14 +284,14 @@ __device__ unsigned long long penult3(uint32_t C, int Wd, const uint32_t* A, int
         const uint32_t ex = __shfl_sync(kFull, excl, w);
         if (j < total) {
             const int e = w * 32 + (int)__fns(cw, 0, (int)(j - ex) + 1);
-            // Ce = C & N(e): with upper rows the elements above e, with
-            // symmetric rows all neighbours of e in C
+            // Ce = C & N(e): upper rows hold nothing below e's group
+            const int elo = PV ? glo : max(glo, e >> 7);
             uint32_t Ce[WM];
             const uint4* Ae4 = (const uint4*)(A + (int64_t)e * RS);
             const uint4* C4 = (const uint4*)sC;
 #pragma unroll
             for (int q = 0; q < WM / 4; ++q) {
-                if (q < glo || q > ghi) {
+                if (q < elo || q > ghi) {
                     Ce[4 * q] = Ce[4 * q + 1] = Ce[4 * q + 2] = Ce[4 * q + 3] = 0u;
                     continue;
                 }
@@ -292,45 +301,35 @@ __device__ unsigned long long penult3(uint32_t C, int Wd, const uint32_t* A, int
                 Ce[4 * q + 2] = cc4.z & a.z;
                 Ce[4 * q + 3] = cc4.w & a.w;
             }
-            uint32_t S = 0, nf = 0;
+            if (wk) wl += (unsigned long long)(4 * (ghi - elo + 1));
+            uint32_t S = 0;
 #pragma unroll
-            for (int q = 0; q < WM; ++q) {
+            for (int q = 0; q < WM; ++q) {  // f in word q of Ce: words q.. of up(f)
+                if (q > xhi) continue;
                 uint32_t bits = Ce[q];
                 while (bits) {
-                    const int f = q * 32 + __ffs(bits) - 1;
+                    const int fb = __ffs(bits) - 1;
                     bits &= bits - 1u;
-                    const uint4* F4 = (const uint4*)(A + (int64_t)f * RS);
+                    const uint32_t* F = A + (int64_t)(q * 32 + fb) * RS;
+                    const uint4* F4 = (const uint4*)F;
                     uint32_t dgr = 0;
 #pragma unroll
-                    for (int r = 0; r < WM / 4; ++r) {
-                        if (r < glo || r > ghi) continue;
+                    for (int r = q / 4; r < WM / 4; ++r) {
+                        if (r > ghi) continue;
                         const uint4 a = F4[r];
-                        dgr += (uint32_t)(__popc(Ce[4 * r] & a.x) + __popc(Ce[4 * r + 1] & a.y) +
-                                          __popc(Ce[4 * r + 2] & a.z) + __popc(Ce[4 * r + 3] & a.w));
+                        const uint32_t ax = 4 * r + 0 < q ? 0u : (4 * r + 0 == q ? (PV ? a.x & cc::mask_above(fb) : a.x) : a.x);
+                        const uint32_t ay = 4 * r + 1 < q ? 0u : (4 * r + 1 == q ? (PV ? a.y & cc::mask_above(fb) : a.y) : a.y);
+                        const uint32_t az = 4 * r + 2 < q ? 0u : (4 * r + 2 == q ? (PV ? a.z & cc::mask_above(fb) : a.z) : a.z);
+                        const uint32_t aw = 4 * r + 3 < q ? 0u : (4 * r + 3 == q ? (PV ? a.w & cc::mask_above(fb) : a.w) : a.w);
+                        dgr += (uint32_t)(__popc(Ce[4 * r] & ax) + __popc(Ce[4 * r + 1] & ay) +
+                                          __popc(Ce[4 * r + 2] & az) + __popc(Ce[4 * r + 3] & aw));
                     }
                     S += dgr;
-                    ++nf;
+                    if (wk) wl += (unsigned long long)(xhi + 1 - q);
                 }
             }
-            if (PV) {  // S = 2 T(e): twice the edges inside N(e) & C
-                const uint32_t T = S / 2u;
-                tot += T;
-                if (T) pv_add(pvlo, pvhi, e, T);
-            } else {
-                tot += S;
-            }
-            if (wk) {
-                // work of the ordered search this replaces: forming the child's
-                // set and one row operation per member above e
-                uint32_t up = nf;
-                if (PV) {
-                    up = 0;
-#pragma unroll
-                    for (int q = 0; q < WM; ++q)
-                        up += (uint32_t)__popc(q < (e >> 5) ? 0u : (q == (e >> 5) ? Ce[q] & cc::mask_above(e & 31) : Ce[q]));
-                }
-                wl += (unsigned long long)(up + 1) * (unsigned long long)Wd;
-            }
+            tot += S;
+            if (PV && S) pv_add(pvlo, pvhi, e, S);
         }
     }
     if (wk) *wk += warp_sum64(wl);
