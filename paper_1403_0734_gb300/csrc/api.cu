@@ -74,9 +74,9 @@ kc_status run_count(const kc_graph* g, int k, uint32_t colours, uint64_t seed, u
     const bool dev = (flags & KC_DEVICE_PTRS) != 0;
     const int32_t n = g->n;
     Scratch sc(s);
-    unsigned long long* small = nullptr;  // [0..1] total lo/hi, [2..9] cursors, [10] work
-    KC_TRY(sc.get(&small, 16));
-    KC_CK(cudaMemsetAsync(small, 0, 16 * sizeof(unsigned long long), s));
+    unsigned long long* small = nullptr;  // [0..1] total lo/hi, [2..15] cursors, [16] work
+    KC_TRY(sc.get(&small, 24));
+    KC_CK(cudaMemsetAsync(small, 0, 24 * sizeof(unsigned long long), s));
 
     // outputs: write permuted results straight into device outputs, else into temps
     unsigned long long* out_pv = nullptr;
@@ -132,9 +132,10 @@ kc_status run_count(const kc_graph* g, int k, uint32_t colours, uint64_t seed, u
         a.total = small;
         a.pv = pv_rank;
         a.po = po_rank;
-        a.work = g_work_enabled ? small + 10 : nullptr;
+        a.work = g_work_enabled ? small + 16 : nullptr;
         a.part = part;
         a.nparts = nparts;
+        a.sc = &sc;
         KC_TRY(count_launch(g, a, small + 2, heavy, hw, s));
         if (pv_rank) {
             k_permute_u64<<<grid1d(n), 256, 0, s>>>(pv_rank, g->perm, n, out_pv);
@@ -150,13 +151,13 @@ kc_status run_count(const kc_graph* g, int k, uint32_t colours, uint64_t seed, u
         KC_CK(cudaMemcpyAsync(total, small, 2 * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
         return KC_OK;
     }
-    unsigned long long th[11] = {0};
+    unsigned long long th[17] = {0};
     KC_CK(cudaMemcpyAsync(th, small, sizeof(th), cudaMemcpyDeviceToHost, s));
     KC_TRY(copy_out_u64(per_vertex, out_pv, n, false, s));
     KC_TRY(copy_out_u64(per_owner, out_po, n, false, s));
     KC_CK(cudaStreamSynchronize(s));
     *total = th[0];
-    if (g_work_enabled) g_last_work = th[10];
+    if (g_work_enabled) g_last_work = th[16];
     return th[1] ? KC_EOVERFLOW : KC_OK;
 }
 
@@ -341,6 +342,7 @@ kc_status kc_footprint(const kc_graph* g, int k, int per_vertex, int per_owner, 
     if (k >= 3) {
         int64_t slot_words = 0;
         b += (uint64_t)kc::heavy_scratch_words(g, k, &slot_words) * 4;
+        b += (uint64_t)kc::split_scratch_words(g, k) * 4;
     }
     *bytes = b;
     return KC_OK;
@@ -411,6 +413,7 @@ kc_status kc_count_batch(const kc_graph* const* gs, int ng, int k, unsigned flag
     a.pv = nullptr;
     a.po = nullptr;
     a.work = nullptr;
+    a.sc = &sc;
     std::vector<int64_t> host_tables;
     KC_TRY(kc::count_batch_launch(gs, ng, a, dd, tables, small, heavy, hw, host_tables, s));
     std::vector<unsigned long long> th((size_t)(2 * ng));

@@ -52,7 +52,8 @@ kc_status sct_launch_slot(int slot, int Wh, const cc::Ctx& c, bool pv, bool col,
                           int64_t heavy_words, cudaStream_t s);
 bool dfs_reg_supported(int k);
 kc_status tri_launch_slot(int slot, int Wh, const cc::Ctx& c, bool pv, cudaStream_t s);
-kc_status dfs_reg_launch(const cc::Ctx& c, int W, bool pv, bool col, cudaStream_t s);
+kc_status dfs_reg_launch(const cc::Ctx& c, int W, bool pv, bool col, Scratch* sc, cudaStream_t s);
+int64_t dfs_tile_words(int W, int k, int64_t items);
 
 kc_status set_smem_max_words(int64_t v)
 {
@@ -441,7 +442,8 @@ int warps_for_width(int W)
 // the shared-memory limit), slots 1..5 = shared-memory rows of 32, 16, 8, 4, 2
 // words, slot 6 = one word (registers).  Wh is the global-tile row width.
 template <bool PV, bool COL>
-kc_status launch_slot_dfs(int slot, int Wh, const Ctx& c, uint32_t* heavy, int64_t heavy_words, cudaStream_t s)
+kc_status launch_slot_dfs(int slot, int Wh, const Ctx& c, uint32_t* heavy, int64_t heavy_words, Scratch* sc,
+                          cudaStream_t s)
 {
     if (c.nitems <= 0) return KC_OK;
     const int sms = num_sms();
@@ -465,7 +467,7 @@ kc_status launch_slot_dfs(int slot, int Wh, const Ctx& c, uint32_t* heavy, int64
         return KC_OK;
     }
     const int W = slot_words(slot);
-    if (dfs_reg_supported(k)) return dfs_reg_launch(c, W, PV, COL, s);  // register-resident search
+    if (dfs_reg_supported(k)) return dfs_reg_launch(c, W, PV, COL, sc, s);  // register-resident search
     const int NW = warps_for_width(W);
     const Layout lay = make_layout(W, W + 1, NW, levels, PV, COL);
     const size_t smem = (size_t)lay.total * 4;
@@ -478,16 +480,16 @@ kc_status launch_slot_dfs(int slot, int Wh, const Ctx& c, uint32_t* heavy, int64
 }
 
 kc_status launch_slot(int slot, int Wh, const Ctx& c, bool pv, bool col, uint32_t* heavy, int64_t heavy_words,
-                      cudaStream_t s)
+                      Scratch* sc, cudaStream_t s)
 {
     if (c.k == 3 && !col && tri_enabled()) return tri_launch_slot(slot, Wh, c, pv, s);  // no bitmaps for k = 3
     if (count_algo() == KC_ALGO_PIVOT) return sct_launch_slot(slot, Wh, c, pv, col, heavy, heavy_words, s);
     if (pv) {
         if (col) return KC_ENOTSUP;
-        return launch_slot_dfs<true, false>(slot, Wh, c, heavy, heavy_words, s);
+        return launch_slot_dfs<true, false>(slot, Wh, c, heavy, heavy_words, sc, s);
     }
-    if (col) return launch_slot_dfs<false, true>(slot, Wh, c, heavy, heavy_words, s);
-    return launch_slot_dfs<false, false>(slot, Wh, c, heavy, heavy_words, s);
+    if (col) return launch_slot_dfs<false, true>(slot, Wh, c, heavy, heavy_words, sc, s);
+    return launch_slot_dfs<false, false>(slot, Wh, c, heavy, heavy_words, sc, s);
 }
 
 Ctx base_ctx(const CountArgs& a)
@@ -563,6 +565,18 @@ int64_t heavy_scratch_words_w(int W, int k, int64_t nheavy, int64_t* slot_words)
     return lay.total * slots;
 }
 
+int64_t split_scratch_words(const kc_graph* g, int k)
+{
+    if (count_algo() != KC_ALGO_DFS || !dfs_reg_supported(k)) return 0;
+    int64_t words = 0;
+    for (int slot = 1; slot < kOwnerSlots - 1; ++slot) {
+        int64_t q0 = 0, q1 = 0;
+        class_range(g, k, slot, &q0, &q1);
+        words += dfs_tile_words(slot_words(slot), k, q1 - q0);
+    }
+    return words;
+}
+
 int64_t heavy_scratch_words(const kc_graph* g, int k, int64_t* slot_words)
 {
     int64_t q0 = 0, q1 = 0;
@@ -589,7 +603,7 @@ kc_status count_launch(const kc_graph* g, const CountArgs& a, unsigned long long
         c.qstride = nparts;
         c.nitems = span > part ? (span - part + nparts - 1) / nparts : 0;
         c.cursor = cursors + slot;
-        KC_TRY(launch_slot(slot, Wh, c, a.per_vertex, col, heavy_scratch, heavy_words, s));
+        KC_TRY(launch_slot(slot, Wh, c, a.per_vertex, col, heavy_scratch, heavy_words, a.sc, s));
     }
     return KC_OK;
 }
@@ -626,7 +640,7 @@ kc_status count_batch_launch(const kc_graph* const* gs, int ng, const CountArgs&
         c.gpre = c.gq0 + ng;
         c.nitems = host_tables[(size_t)(slot * per + ng + ng)];
         c.cursor = cursors + slot;
-        KC_TRY(launch_slot(slot, Wh, c, false, col, heavy_scratch, heavy_words, s));
+        KC_TRY(launch_slot(slot, Wh, c, false, col, heavy_scratch, heavy_words, a.sc, s));
     }
     return KC_OK;
 }

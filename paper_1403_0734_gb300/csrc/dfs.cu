@@ -542,8 +542,46 @@ __device__ unsigned long long dfs_reg(uint32_t c0, int need0, int Wd, const uint
     return total;
 }
 
-template <bool PV, bool COL, int WM>
-__global__ void __launch_bounds__(256, 4) k_dfs_reg(Ctx cb, int W, int R, int clo, int chi)
+// The sub-tree below a candidate set C (lane w holds word w; cnt elements,
+// the lowest in word fw) when `need` >= 2 vertices are still to be chosen:
+// edges of G[C] (need 2), triangles (need 3), a compact copy (small C), or
+// the register search below (need >= 4).  Credits the members met inside.
+template <bool PV, int WM>
+__device__ __forceinline__ unsigned long long subtree(uint32_t C, int cnt, int need, int fw, int Wd, const uint32_t* A,
+                                                      int RS, uint32_t* pvlo, uint32_t* pvhi, uint32_t* sC, int lane,
+                                                      unsigned long long* wk, int clo, int chi)
+{
+    const bool compact = cnt >= clo && cnt <= chi;
+    if (need == 2) return (unsigned long long)leaf2_any<PV, WM>(C, fw, Wd, A, RS, pvlo, pvhi, lane, wk);
+    if (compact) return compact_count<PV>(C, cnt, need, A, RS, pvlo, pvhi, lane, wk);
+    if (WM >= 4 && need == 3) return penult3<PV, (WM >= 4 ? WM : 4)>(C, Wd, A, RS, pvlo, pvhi, sC, lane, wk);
+    return dfs_reg<PV, WM>(C, need, Wd, A, RS, pvlo, pvhi, sC, lane, wk, clo, chi);
+}
+
+// Row e of G+(u) above e, one word per lane (lane w: word w).
+__device__ __forceinline__ uint32_t upper_word(const uint32_t* A, int RS, int e, int Wd, int lane)
+{
+    const int we = e >> 5;
+    uint32_t v = (lane >= we && lane < Wd) ? A[(int64_t)e * RS + lane] : 0u;
+    if (lane == we) v &= mask_above(e & 31);
+    return v;
+}
+
+// Work items of one owner u of the class: its search is cut into tasks --
+// first-level vertices e1 for k <= 5; pairs (e1, e2), e2 a neighbour of e1
+// above it, for k >= 6 (the second level of the heavy-owner split, Sec. 7:
+// (k-2)-cliques of G+(u) counted under the key (u, e1), each of those cut
+// again by e2).  Item i of the class launch is (owner i / R, part i % R);
+// the R parts of an owner share its task counter, so they stay balanced
+// however uneven the tasks are.
+//   TILE = false: R == 1; the item's CTA builds G+(u) in shared memory (its
+//       warps together) and hands out the tasks from a shared counter.
+//   TILE = true: G+(u) was built once, by k_tile_build, into the owner's
+//       global tile; every part copies it into shared memory and takes tasks
+//       from the owner's global counter.
+template <bool PV, bool COL, int WM, bool TILE>
+__global__ void __launch_bounds__(256, 4) k_dfs_reg(Ctx cb, int W, int R, int clo, int chi, const uint32_t* tiles,
+                                                  int64_t tile_words, unsigned int* task_ctr)
 {
     extern __shared__ __align__(16) uint32_t smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, NW = blockDim.x >> 5;
@@ -554,48 +592,104 @@ __global__ void __launch_bounds__(256, 4) k_dfs_reg(Ctx cb, int W, int R, int cl
     uint32_t* pvlo = smem + lay.pvlo;
     uint32_t* pvhi = smem + lay.pvhi;
     uint32_t* sA = smem + lay.A;
+    // task prefix over first-level vertices (k >= 6): aliases the span table,
+    // which is only used while the rows are built
+    unsigned int* sP = smem + lay.sbits;
     __shared__ __align__(16) uint32_t s_c[8][32];  // per-warp candidate-set buffer
-    __shared__ int s_next;
+    __shared__ unsigned int s_next;
     __shared__ unsigned long long s_tot, s_wk;
     __shared__ long long s_item;
     const int r0 = cb.k - 1;
+    const bool pairs = r0 >= 5;  // k >= 6: tasks are (e1, e2)
 
     for (;;) {
         if (threadIdx.x == 0) s_item = (long long)atomicAdd(cb.cursor, 1ull);
         __syncthreads();
-        const int part = (int)(s_item % R);
+        const int64_t oi = s_item / R;
         Ctx c;
         int32_t r;
-        if (!cc::resolve(cb, (int64_t)(s_item / R), c, r)) break;
+        if (!cc::resolve(cb, oi, c, r)) break;
         const int64_t b = c.offp[r];
         const int d = (int)(c.offp[r + 1] - b);
         const int Wd = (d + 31) >> 5;
-        const int32_t ur = COL ? c.perm[r] : 0;
         for (int j = threadIdx.x; j < d; j += blockDim.x) {
             const int32_t x = c.adjp[b + j];
             sL[j] = x;
-            if (COL) sCol[j] = cc::sample_label(c, ur, c.perm[x]);
-            if (PV) {
-                pvlo[j] = 0u;
-                pvhi[j] = 0u;
-            }
+            if (!TILE && COL) sCol[j] = cc::sample_label(c, c.perm[r], c.perm[x]);
         }
-        for (int64_t j = threadIdx.x; j < (int64_t)d * RS; j += blockDim.x) sA[j] = 0u;
+        if (TILE) {
+            const uint4* src = (const uint4*)(tiles + oi * tile_words);
+            uint4* dst = (uint4*)sA;
+            for (int64_t j = threadIdx.x; j < ((int64_t)d * RS + 3) / 4; j += blockDim.x) dst[j] = src[j];
+        } else {
+            for (int64_t j = threadIdx.x; j < (int64_t)d * RS; j += blockDim.x) sA[j] = 0u;
+        }
         if (threadIdx.x == 0) {
-            s_next = 0;
+            s_next = 0u;
             s_tot = 0ull;
             s_wk = 0ull;
         }
         __syncthreads();
-        cc::SpanTable T{smem + lay.sbits, (uint16_t*)(smem + lay.spre), 0, 0};
-        cc::span_table_build(T, sL, d, kSpanWords);
-        cc::build_rows<PV, COL>(c, sL, sCol, d, sA, RS, wid, NW, lane, ur, &T);
-        __syncthreads();
+        if (!TILE) {
+            const int32_t ur = COL ? c.perm[r] : 0;
+            cc::SpanTable T{smem + lay.sbits, (uint16_t*)(smem + lay.spre), 0, 0};
+            cc::span_table_build(T, sL, d, kSpanWords);
+            cc::build_rows<PV, COL>(c, sL, sCol, d, sA, RS, wid, NW, lane, ur, &T);
+            __syncthreads();
+        }
+        if (PV)
+            for (int j = threadIdx.x; j < d; j += blockDim.x) {
+                pvlo[j] = 0u;
+                pvhi[j] = 0u;
+            }
+        unsigned int ntasks = (unsigned int)d;
+        if (pairs) {  // sP[e] = number of pairs (e', e2) with e' < e
+            for (int e = threadIdx.x; e < d; e += blockDim.x) {
+                const uint32_t* Ae = sA + (int64_t)e * RS;
+                unsigned int cnt = (unsigned int)__popc(Ae[e >> 5] & mask_above(e & 31));
+                for (int w = (e >> 5) + 1; w < Wd; ++w) cnt += (unsigned int)__popc(Ae[w]);
+                sP[e] = cnt;
+            }
+            __syncthreads();
+            // exclusive scan of sP[0..d) by warp 0 (d <= 1024: 32 per lane)
+            if (wid == 0) {
+                const int per = (d + 31) / 32;
+                unsigned int loc = 0;
+                for (int q = 0; q < per; ++q) {
+                    const int e = lane * per + q;
+                    if (e < d) loc += sP[e];
+                }
+                unsigned int inc = loc;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const unsigned int t = __shfl_up_sync(kFull, inc, o);
+                    if (lane >= o) inc += t;
+                }
+                unsigned int run = inc - loc;
+                for (int q = 0; q < per; ++q) {
+                    const int e = lane * per + q;
+                    if (e < d) {
+                        const unsigned int v = sP[e];
+                        sP[e] = run;
+                        run += v;
+                    }
+                }
+                if (lane == 31) sP[d] = inc;
+            }
+            __syncthreads();
+            ntasks = sP[d];
+        }
+        unsigned int* ctr = TILE ? task_ctr + oi : &s_next;
 
         unsigned long long wtot = 0, wk = 0;
         unsigned long long* wkp = c.work ? &wk : nullptr;
-        if (r0 == 2) {  // k = 3: edges of G+(u)
-            for (int e = part + wid * R; e < d; e += NW * R) {
+        for (;;) {
+            unsigned int t = 0;
+            if (lane == 0) t = atomicAdd(ctr, 1u);
+            t = __shfl_sync(kFull, t, 0);
+            if (t >= ntasks) break;
+            if (r0 == 2) {  // k = 3: edges of G+(u) from e1 = t
+                const int e = (int)t;
                 const uint32_t* Ae = sA + (int64_t)e * RS;
                 const int we = e >> 5, be = e & 31;
                 uint32_t up = 0, all = 0;
@@ -611,32 +705,52 @@ __global__ void __launch_bounds__(256, 4) k_dfs_reg(Ctx cb, int W, int R, int cl
                     if (lane == 0 && all) pv_add(pvlo, pvhi, e, all);
                 }
                 if (wkp) wk += (unsigned long long)(PV ? Wd : Wd - we);
+                continue;
             }
-        } else {
-            const int need0 = r0 - 1;
-            for (;;) {
-                int e1 = 0;
-                if (lane == 0) e1 = part + R * atomicAdd(&s_next, 1);
-                e1 = __shfl_sync(kFull, e1, 0);
-                if (e1 >= d) break;
-                const int we = e1 >> 5, be = e1 & 31;
-                uint32_t c0 = 0u;
-                if (lane >= we && lane < Wd) {
-                    c0 = sA[(int64_t)e1 * RS + lane];
-                    if (lane == we) c0 &= mask_above(be);
+            int e1, e2 = -1;
+            uint32_t cset;
+            int need;
+            if (!pairs) {
+                e1 = (int)t;
+                cset = upper_word(sA, RS, e1, Wd, lane);
+                need = r0 - 1;
+                if (wkp) wk += (unsigned long long)(Wd - (e1 >> 5));
+            } else {
+                // e1: the last vertex whose prefix is <= t (binary search in sP)
+                int lo = 0, hi = d;
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (sP[mid] <= t) lo = mid; else hi = mid;
                 }
-                const int cnt = (int)__reduce_add_sync(kFull, (unsigned)__popc(c0));
-                if (wkp) wk += (unsigned long long)(Wd - we);
-                if (cnt < need0) continue;
-                const bool compact = cnt >= clo && cnt <= chi;
-                const unsigned long long sub =
-                    need0 == 2 ? (unsigned long long)leaf2_any<PV, WM>(c0, we, Wd, sA, RS, pvlo, pvhi, lane, wkp)
-                    : compact  ? compact_count<PV>(c0, cnt, need0, sA, RS, pvlo, pvhi, lane, wkp)
-                    : (WM >= 4 && need0 == 3)
-                        ? penult3<PV, (WM >= 4 ? WM : 4)>(c0, Wd, sA, RS, pvlo, pvhi, s_c[wid], lane, wkp)
-                        : dfs_reg<PV, WM>(c0, need0, Wd, sA, RS, pvlo, pvhi, s_c[wid], lane, wkp, clo, chi);
-                wtot += sub;
-                if (PV && lane == 0 && sub) pv_add(pvlo, pvhi, e1, sub);
+                e1 = lo;
+                const unsigned int j = t - sP[e1];
+                // e2: the j-th element of row e1 above e1
+                const uint32_t u1 = upper_word(sA, RS, e1, Wd, lane);
+                const unsigned int pc = (unsigned int)__popc(u1);
+                unsigned int inc = pc;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const unsigned int x = __shfl_up_sync(kFull, inc, o);
+                    if (lane >= o) inc += x;
+                }
+                const uint32_t hit = __ballot_sync(kFull, inc > j && inc - pc <= j);
+                const int hw = __ffs(hit) - 1;
+                const uint32_t hv = __shfl_sync(kFull, u1, hw);
+                const unsigned int hx = __shfl_sync(kFull, inc - pc, hw);
+                e2 = hw * 32 + (int)__fns(hv, 0, (int)(j - hx) + 1);
+                cset = u1 & upper_word(sA, RS, e2, Wd, lane);
+                need = r0 - 2;
+                if (wkp) wk += (unsigned long long)(2 * (Wd - (e1 >> 5)));
+            }
+            const int cnt = (int)__reduce_add_sync(kFull, (unsigned)__popc(cset));
+            if (cnt < need) continue;
+            const int fw = __ffs(__ballot_sync(kFull, cset != 0u)) - 1;
+            const unsigned long long sub =
+                subtree<PV, WM>(cset, cnt, need, fw, Wd, sA, RS, pvlo, pvhi, s_c[wid], lane, wkp, clo, chi);
+            wtot += sub;
+            if (PV && lane == 0 && sub) {
+                pv_add(pvlo, pvhi, e1, sub);
+                if (e2 >= 0) pv_add(pvlo, pvhi, e2, sub);
             }
         }
         if (lane == 0 && wtot) atomicAdd(&s_tot, wtot);
@@ -645,7 +759,7 @@ __global__ void __launch_bounds__(256, 4) k_dfs_reg(Ctx cb, int W, int R, int cl
         const unsigned long long tot = s_tot;
         if (threadIdx.x == 0) {
             add_total(c.total, tot);
-            if (c.po && tot) atomicAdd(&c.po[r], tot);  // R parts add up
+            if (c.po && tot) atomicAdd(&c.po[r], tot);  // the R parts add up
             if (PV && tot) atomicAdd(&c.pv[r], tot);
             if (c.work && s_wk) atomicAdd(c.work, s_wk);
         }
@@ -654,6 +768,47 @@ __global__ void __launch_bounds__(256, 4) k_dfs_reg(Ctx cb, int W, int R, int cl
                 const unsigned long long v = ((unsigned long long)pvhi[j] << 32) | pvlo[j];
                 if (v) atomicAdd(&c.pv[sL[j]], v);
             }
+        __syncthreads();
+    }
+}
+
+// G+(u) of every owner of the class, built once into its global tile (the
+// shared-memory row layout, d rows of RS words), for the split search.
+template <bool PV, bool COL, int WM>
+__global__ void __launch_bounds__(256) k_tile_build(Ctx cb, int W, uint32_t* tiles, int64_t tile_words)
+{
+    extern __shared__ __align__(16) uint32_t smem[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, NW = blockDim.x >> 5;
+    const int RS = row_stride(W, WM);
+    const RLayout lay = make_rlayout(W, RS, false, COL, NW);
+    int32_t* sL = (int32_t*)(smem + lay.L);
+    uint32_t* sCol = smem + lay.col;
+    uint32_t* sA = smem + lay.A;
+    __shared__ long long s_item;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (long long)atomicAdd(cb.cursor, 1ull);
+        __syncthreads();
+        const int64_t oi = s_item;
+        Ctx c;
+        int32_t r;
+        if (!cc::resolve(cb, oi, c, r)) break;
+        const int64_t b = c.offp[r];
+        const int d = (int)(c.offp[r + 1] - b);
+        const int32_t ur = COL ? c.perm[r] : 0;
+        for (int j = threadIdx.x; j < d; j += blockDim.x) {
+            const int32_t x = c.adjp[b + j];
+            sL[j] = x;
+            if (COL) sCol[j] = cc::sample_label(c, ur, c.perm[x]);
+        }
+        for (int64_t j = threadIdx.x; j < (int64_t)d * RS; j += blockDim.x) sA[j] = 0u;
+        __syncthreads();
+        cc::SpanTable T{smem + lay.sbits, (uint16_t*)(smem + lay.spre), 0, 0};
+        cc::span_table_build(T, sL, d, kSpanWords);
+        cc::build_rows<PV, COL>(c, sL, sCol, d, sA, RS, wid, NW, lane, ur, &T);
+        __syncthreads();
+        uint4* dst = (uint4*)(tiles + oi * tile_words);
+        const uint4* src = (const uint4*)sA;
+        for (int64_t j = threadIdx.x; j < ((int64_t)d * RS + 3) / 4; j += blockDim.x) dst[j] = src[j];
         __syncthreads();
     }
 }
@@ -672,32 +827,72 @@ int parts_per_owner(int W, int k)
     return 1;
 }
 
-// Launch the shared-memory class of width W (words) over queue range [q0, q1).
-kc_status dfs_reg_launch(const cc::Ctx& c, int W, bool pv, bool col, cudaStream_t s)
+// Tile memory (32-bit words) a class of width W with `items` owners needs for
+// the split search at k (0: no split).
+int64_t dfs_tile_words(int W, int k, int64_t items)
+{
+    if (parts_per_owner(W, k) <= 1 || items <= 0) return 0;
+    const int WM = W <= 16 ? W : 0;
+    const int64_t per = 32LL * W * row_stride(W, WM);
+    return per * items + (items + 3);  // tiles, then the task counters
+}
+
+// Launch the shared-memory class of width W (words) over its queue range.
+// With an allocator and R > 1 the owners' rows are built once into global
+// tiles (k_tile_build) and the R parts copy them; without one (the
+// allocation-free entry point) every owner is searched by one CTA.
+kc_status dfs_reg_launch(const cc::Ctx& c, int W, bool pv, bool col, Scratch* sc, cudaStream_t s)
 {
     const int sms = num_sms();
-    const int R = parts_per_owner(W, c.k);
+    int R = parts_per_owner(W, c.k);
+    if (!sc) R = 1;
     const int NW = W <= 4 ? 4 : 8;
     const int WM = W <= 16 ? W : 0;  // widest class keeps the generic last level
-    const RLayout lay = make_rlayout(W, row_stride(W, WM), pv, col, NW);
+    const int RS = row_stride(W, WM);
+    const RLayout lay = make_rlayout(W, RS, pv, col, NW);
     const size_t smem = (size_t)lay.total * 4;
-    auto pick = [&](auto kern) -> kc_status {
+    uint32_t* tiles = nullptr;
+    unsigned int* ctr = nullptr;
+    const int64_t tile_words = 32LL * W * RS;
+    if (R > 1) {
+        KC_TRY(sc->get(&tiles, dfs_tile_words(W, c.k, c.nitems)));
+        ctr = tiles + tile_words * c.nitems;
+        KC_CK(cudaMemsetAsync(ctr, 0, (size_t)c.nitems * sizeof(unsigned int), s));
+    }
+    auto pick = [&](auto kern, auto build) -> kc_status {
+        if (R > 1) {
+            // the build pass takes owners from the class cursor; the search
+            // pass then counts items from a second cursor (the slot's next word)
+            const RLayout bl = make_rlayout(W, RS, false, col, 8);
+            const size_t bsm = (size_t)bl.total * 4;
+            KC_CK(cc::allow_smem(build, bsm));
+            const int bgrid = (int)std::min<int64_t>(c.nitems, (int64_t)sms * cc::blocks_per_sm(build, 256, bsm));
+            build<<<bgrid, 256, bsm, s>>>(c, W, tiles, tile_words);
+            KC_LAUNCHED();
+        }
+        cc::Ctx cs = c;
+        if (R > 1) cs.cursor = c.cursor + kc::kOwnerSlots;  // a fresh zeroed cursor for the search
         KC_CK(cc::allow_smem(kern, smem));
         const int grid =
             (int)std::min<int64_t>(c.nitems * R, (int64_t)sms * cc::blocks_per_sm(kern, NW * 32, smem));
-        kern<<<grid, NW * 32, smem, s>>>(c, W, R, g_compact_lo, g_compact_hi);
+        kern<<<grid, NW * 32, smem, s>>>(cs, W, R, g_compact_lo, g_compact_hi, tiles, tile_words, ctr);
         KC_LAUNCHED();
         return KC_OK;
     };
     auto by_width = [&](auto pv_t, auto col_t) -> kc_status {
         constexpr bool P = decltype(pv_t)::value, Q = decltype(col_t)::value;
+        const bool split = R > 1;
+#define KC_DFS_PICK(WMV)                                                                              \
+    return split ? pick(k_dfs_reg<P, Q, WMV, true>, k_tile_build<P, Q, WMV>)                          \
+                 : pick(k_dfs_reg<P, Q, WMV, false>, k_tile_build<P, Q, WMV>)
         switch (WM) {
-        case 2: return pick(k_dfs_reg<P, Q, 2>);
-        case 4: return pick(k_dfs_reg<P, Q, 4>);
-        case 8: return pick(k_dfs_reg<P, Q, 8>);
-        case 16: return pick(k_dfs_reg<P, Q, 16>);
-        default: return pick(k_dfs_reg<P, Q, 0>);
+        case 2: KC_DFS_PICK(2);
+        case 4: KC_DFS_PICK(4);
+        case 8: KC_DFS_PICK(8);
+        case 16: KC_DFS_PICK(16);
+        default: KC_DFS_PICK(0);
         }
+#undef KC_DFS_PICK
     };
     if (pv) return col ? KC_ENOTSUP : by_width(std::true_type{}, std::false_type{});
     return col ? by_width(std::false_type{}, std::true_type{}) : by_width(std::false_type{}, std::false_type{});

@@ -54,6 +54,9 @@ constexpr int kClassWords[kNumSmemClasses] = {1, 2, 4, 8, 16, 32};
 // (global tiles), 1..5 = shared-memory rows of 32, 16, 8, 4, 2 words,
 // 6 = one word (registers).
 constexpr int kOwnerSlots = 7;
+// Zeroed cursor words a count needs: one per owner slot, and a second one
+// per slot for the search pass of a split class.
+constexpr int kCursorWords = 2 * kOwnerSlots;
 
 // ---------------------------------------------------------- graph handle
 
@@ -112,9 +115,10 @@ struct CountArgs {
     unsigned long long* po;     // [n] rank space, nullable
     unsigned long long* work;   // [1] bitmap word-operations executed, nullable
     int part = 0, nparts = 1;   // count only owners at queue positions = part (mod nparts)
+    struct Scratch* sc = nullptr;  // allocator for the split search's tiles (null: no split)
 };
 
-// cursors: kOwnerSlots zeroed counters.
+// cursors: kCursorWords zeroed counters.
 kc_status count_launch(const kc_graph* g, const CountArgs& a, unsigned long long* cursors,
                        uint32_t* heavy_scratch, int64_t heavy_words, cudaStream_t s);
 
@@ -207,5 +211,9 @@ struct DeviceGuard {
 // Words of global scratch the heavy (global-bitmap) class needs for k under
 // the current settings; *slot_words receives the size of one tile slot.
 int64_t heavy_scratch_words(const kc_graph* g, int k, int64_t* slot_words);
+
+// Words of global tiles the split search of the shared-memory classes needs
+// for k (allocated by the count from its Scratch).
+int64_t split_scratch_words(const kc_graph* g, int k);
 
 }  // namespace kc

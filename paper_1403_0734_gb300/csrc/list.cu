@@ -294,9 +294,9 @@ kc_status list_run(const kc_graph* g, int k, unsigned flags, int32_t* buf, int64
     *listed = 0;
     if (n == 0) return KC_OK;
     Scratch sc(s);
-    unsigned long long* small = nullptr;  // [0..1] total, [2..9] cursors
-    KC_TRY(sc.get(&small, 16));
-    KC_CK(cudaMemsetAsync(small, 0, 16 * sizeof(unsigned long long), s));
+    unsigned long long* small = nullptr;  // [0..1] total, [2..15] cursors
+    KC_TRY(sc.get(&small, 24));
+    KC_CK(cudaMemsetAsync(small, 0, 24 * sizeof(unsigned long long), s));
 
     // queue (owners by d+ descending) and per-owner counts, on the host
     std::vector<int32_t> hq(n);
@@ -329,6 +329,7 @@ kc_status list_run(const kc_graph* g, int k, unsigned flags, int32_t* buf, int64
         a.pv = nullptr;
         a.po = po;
         a.work = nullptr;
+        a.sc = &sc;
         KC_TRY(count_launch(g, a, small + 2, heavy, hw, s));
         KC_CK(cudaMemcpyAsync(cnt.data(), po, (size_t)n * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
     }
@@ -379,7 +380,7 @@ kc_status list_run(const kc_graph* g, int k, unsigned flags, int32_t* buf, int64
         }
         KC_CK(cudaMemcpyAsync(doff, hoff.data(), hoff.size() * sizeof(unsigned long long), cudaMemcpyHostToDevice,
                               s));
-        KC_CK(cudaMemsetAsync(cursors, 0, kOwnerSlots * sizeof(unsigned long long), s));
+        KC_CK(cudaMemsetAsync(cursors, 0, kCursorWords * sizeof(unsigned long long), s));
         Ctx base;
         base.offp = g->offp;
         base.adjp = g->adjp;

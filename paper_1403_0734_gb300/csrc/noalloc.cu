@@ -93,7 +93,7 @@ extern "C" kc_status kc_count_static(const kc_graph* g, int k, unsigned flags, u
 
     void* base = nullptr;
     KC_TRY(scratch_address(g->device, &base));
-    unsigned long long* small = (unsigned long long*)base;  // [0..1] total, [2..9] cursors
+    unsigned long long* small = (unsigned long long*)base;  // [0..1] total, [2..15] cursors
     uint32_t* tiles = (uint32_t*)((char*)base + kSmallBytes);
     const int64_t tile_words = (int64_t)((kStaticScratchBytes - kSmallBytes) / sizeof(uint32_t));
 
@@ -116,6 +116,7 @@ extern "C" kc_status kc_count_static(const kc_graph* g, int k, unsigned flags, u
         a.pv = nullptr;
         a.po = nullptr;
         a.work = nullptr;
+        a.sc = nullptr;  // no allocator: every owner is searched by one CTA (no split tiles)
         KC_TRY(kc::count_launch(g, a, small + 2, need > 0 ? tiles : nullptr, use_words, s));
     }
     if (dev_out) {
