@@ -274,7 +274,8 @@ kc_status kc_count_part(const kc_graph* g, int k, int part, int nparts, unsigned
  * kc_count_batch -- kc_count's total for each of ng graphs (all on one
  * device) in a single launch sequence: the owners of all graphs form one
  * queue per owner class, so many small, uneven graphs fill the GPU together
- * instead of one launch each.
+ * instead of one launch each.  Uses the plan (kc_set_tuning) attached to
+ * gs[0] for k without per-vertex output, if any.
  *   gs      host array of ng graph handles
  *   totals  out: host array of ng counts, or with KC_DEVICE_PTRS a device
  *           array of 2*ng words (low, high per graph)
@@ -321,6 +322,50 @@ kc_status kc_count_batch(const kc_graph* const* gs, int ng, int k, unsigned flag
 #define KC_ALGO_DFS   1
 kc_status kc_set_param(int param, int64_t value);
 kc_status kc_get_param(int param, int64_t* value);
+
+/*
+ * Autotuning (batching, owner classes).  The counting kernels take owners in
+ * classes by the width of their bitmap row (the queue groups of kc_export):
+ *   class 0: |Gamma+| above the shared-memory limit (global-memory tiles),
+ *   classes 1..5: rows of 32, 16, 8, 4, 2 words (shared memory),
+ *   class 6: rows of one word (registers).
+ * For each class a plan names the Reduce 3 counter (KC_ALGO_DFS or
+ * KC_ALGO_PIVOT, see KC_PARAM_ALGO) and, for the ordered search of classes
+ * 1..5, the number of CTAs that share one owner (parts: 1 = no split; the
+ * split owners' G+(u) is built once into a global tile).  A plan changes
+ * speed only, never results.
+ */
+typedef struct {
+    int32_t k;           /* the k the plan is for */
+    int32_t per_vertex;  /* 1: for counts with per-vertex output, 0: without */
+    int32_t algo[7];     /* per class: KC_ALGO_DFS or KC_ALGO_PIVOT */
+    int32_t parts[7];    /* per class: CTAs per owner (ordered search), >= 1 */
+    float ms[7];         /* per class: measured sample time of the choice (ms) */
+} kc_tuning;
+
+#define KC_TUNE_PER_VERTEX 0x10u  /* kc_tune: tune for counts with per-vertex output */
+
+/*
+ * kc_tune -- measure, for every owner class of the ng graphs (one graph:
+ * ng = 1), the candidate plans -- the ordered search with 1, 4 or 16 parts
+ * per owner (4 and 16 only for classes of 8+ words at k >= 5) and the
+ * pivoting counter -- on a sample of the class's heaviest owners (its first
+ * owners in queue order, at most 256), and return the fastest in `out`.  The
+ * graphs are not changed (attach the plan with kc_set_tuning).  Runs
+ * synchronously on `stream`.
+ *   k      3..KC_MAX_K (k <= 2 needs no plan: out gets the defaults)
+ *   flags  KC_TUNE_PER_VERTEX
+ * Errors: KC_EINVAL, KC_ENOMEM, KC_ECUDA.
+ */
+kc_status kc_tune(const kc_graph* const* gs, int ng, int k, unsigned flags, void* stream, kc_tuning* out);
+
+/*
+ * kc_set_tuning -- attach a plan to g: later exact counts of g (kc_count,
+ * kc_count_part, kc_list, kc_count_batch with g as its first graph) for the
+ * plan's k and output mode use it.  t = NULL removes every plan of g.
+ * Errors: KC_EINVAL (bad k, algorithm or parts).
+ */
+kc_status kc_set_tuning(kc_graph* g, const kc_tuning* t);
 
 /*
  * kc_count_csr / kc_estimate_csr -- one-shot forms: kc_orient, then kc_count

@@ -118,11 +118,14 @@ kc_status run_count(const kc_graph* g, int k, uint32_t colours, uint64_t seed, u
             KC_TRY(sc.get(&po_rank, n));
             KC_CK(cudaMemsetAsync(po_rank, 0, (size_t)n * sizeof(unsigned long long), s));
         }
+        Plan plan;
+        const bool planned = colours == 0 && !pair && find_plan(g, k, per_vertex != nullptr, &plan);
         int64_t slot_words = 0;
-        const int64_t hw = heavy_scratch_words(g, k, &slot_words);
+        const int64_t hw = heavy_scratch_words(g, k, &slot_words, planned ? &plan : nullptr);
         uint32_t* heavy = nullptr;
         if (hw > 0) KC_TRY(sc.get(&heavy, hw));
         CountArgs a;
+        a.plan = planned ? &plan : nullptr;
         a.k = k;
         a.colours = colours;
         a.seed = seed;
@@ -340,9 +343,12 @@ kc_status kc_footprint(const kc_graph* g, int k, int per_vertex, int per_owner, 
     if (k >= 3) b += arrays * n * 8;           // rank-space accumulators
     if (host_outputs) b += arrays * n * 8;     // staging for the copy back
     if (k >= 3) {
+        kc::Plan plan;
+        const bool planned = kc::find_plan(g, k, per_vertex != 0, &plan);
         int64_t slot_words = 0;
-        b += (uint64_t)kc::heavy_scratch_words(g, k, &slot_words) * 4;
-        b += (uint64_t)kc::split_scratch_words(g, k) * 4;
+        b += (uint64_t)kc::heavy_scratch_words(g, k, &slot_words, planned ? &plan : nullptr) * 4;
+        b += (uint64_t)kc::split_scratch_words(g, k, planned ? &plan : nullptr) * 4;
+        b += 256 * 8;  // alignment of the scratch blocks
     }
     *bytes = b;
     return KC_OK;
@@ -400,11 +406,14 @@ kc_status kc_count_batch(const kc_graph* const* gs, int ng, int k, unsigned flag
     KC_TRY(sc.get(&small, 16 + 2 * (int64_t)ng));
     KC_CK(cudaMemcpyAsync(dd, hd.data(), hd.size() * sizeof(kc::cc::GraphDesc), cudaMemcpyHostToDevice, s));
     KC_CK(cudaMemsetAsync(small, 0, (16 + 2 * (size_t)ng) * sizeof(unsigned long long), s));
+    kc::Plan plan;
+    const bool planned = kc::find_plan(gs[0], k, false, &plan);
     int64_t slot_words = 0;
-    const int64_t hw = kc::heavy_scratch_words_w(Wh, k, nheavy, &slot_words);
+    const int64_t hw = kc::heavy_scratch_words_w(Wh, k, nheavy, &slot_words, planned ? plan.algo[0] : -1);
     uint32_t* heavy = nullptr;
     if (hw > 0) KC_TRY(sc.get(&heavy, hw));
     kc::CountArgs a;
+    a.plan = planned ? &plan : nullptr;
     a.k = k;
     a.colours = 0;
     a.seed = 0;
@@ -430,6 +439,37 @@ kc_status kc_count_batch(const kc_graph* const* gs, int ng, int k, unsigned flag
         if (th[(size_t)(2 * i + 1)]) st = KC_EOVERFLOW;
     }
     return st;
+}
+
+kc_status kc_tune(const kc_graph* const* gs, int ng, int k, unsigned flags, void* stream, kc_tuning* out)
+{
+    if (!gs || ng < 1 || !out || k < 1 || k > KC_MAX_K) return KC_EINVAL;
+    for (int i = 0; i < ng; ++i)
+        if (!gs[i] || gs[i]->device != gs[0]->device) return KC_EINVAL;
+    kc::DeviceGuard dg(gs[0]->device);
+    for (int i = 0; i < ng; ++i) KC_TRY(kc::ready(gs[i]));
+    return kc::tune(gs, ng, k, (flags & KC_TUNE_PER_VERTEX) != 0, (cudaStream_t)stream, out);
+}
+
+kc_status kc_set_tuning(kc_graph* g, const kc_tuning* t)
+{
+    if (!g) return KC_EINVAL;
+    if (!t) {
+        g->tunings.clear();
+        return KC_OK;
+    }
+    if (t->k < 1 || t->k > KC_MAX_K) return KC_EINVAL;
+    for (int i = 0; i < kc::kOwnerSlots; ++i) {
+        if (t->algo[i] != KC_ALGO_DFS && t->algo[i] != KC_ALGO_PIVOT) return KC_EINVAL;
+        if (t->parts[i] < 1 || t->parts[i] > 64) return KC_EINVAL;
+    }
+    for (kc_tuning& x : g->tunings)
+        if (x.k == t->k && (x.per_vertex != 0) == (t->per_vertex != 0)) {
+            x = *t;
+            return KC_OK;
+        }
+    g->tunings.push_back(*t);
+    return KC_OK;
 }
 
 kc_status kc_set_param(int param, int64_t value)

@@ -24,6 +24,7 @@
 // wider owners use the same CTA code on a global-memory tile.
 #include <algorithm>
 #include <climits>
+#include <cstring>
 
 #include "count_common.cuh"
 
@@ -48,12 +49,13 @@ kc_status set_count_algo(int64_t v)
 }
 
 int64_t sct_heavy_words_w(int W, int k, int64_t nheavy);
+int parts_per_owner(int W, int k);
 kc_status sct_launch_slot(int slot, int Wh, const cc::Ctx& c, bool pv, bool col, uint32_t* heavy,
                           int64_t heavy_words, cudaStream_t s);
 bool dfs_reg_supported(int k);
 kc_status tri_launch_slot(int slot, int Wh, const cc::Ctx& c, bool pv, cudaStream_t s);
-kc_status dfs_reg_launch(const cc::Ctx& c, int W, bool pv, bool col, Scratch* sc, cudaStream_t s);
-int64_t dfs_tile_words(int W, int k, int64_t items);
+kc_status dfs_reg_launch(const cc::Ctx& c, int W, bool pv, bool col, Scratch* sc, int parts, cudaStream_t s);
+int64_t dfs_tile_words(int W, int k, int64_t items, int parts);
 
 kc_status set_smem_max_words(int64_t v)
 {
@@ -443,7 +445,7 @@ int warps_for_width(int W)
 // words, slot 6 = one word (registers).  Wh is the global-tile row width.
 template <bool PV, bool COL>
 kc_status launch_slot_dfs(int slot, int Wh, const Ctx& c, uint32_t* heavy, int64_t heavy_words, Scratch* sc,
-                          cudaStream_t s)
+                          int parts, cudaStream_t s)
 {
     if (c.nitems <= 0) return KC_OK;
     const int sms = num_sms();
@@ -467,7 +469,7 @@ kc_status launch_slot_dfs(int slot, int Wh, const Ctx& c, uint32_t* heavy, int64
         return KC_OK;
     }
     const int W = slot_words(slot);
-    if (dfs_reg_supported(k)) return dfs_reg_launch(c, W, PV, COL, sc, s);  // register-resident search
+    if (dfs_reg_supported(k)) return dfs_reg_launch(c, W, PV, COL, sc, parts, s);  // register-resident search
     const int NW = warps_for_width(W);
     const Layout lay = make_layout(W, W + 1, NW, levels, PV, COL);
     const size_t smem = (size_t)lay.total * 4;
@@ -480,16 +482,18 @@ kc_status launch_slot_dfs(int slot, int Wh, const Ctx& c, uint32_t* heavy, int64
 }
 
 kc_status launch_slot(int slot, int Wh, const Ctx& c, bool pv, bool col, uint32_t* heavy, int64_t heavy_words,
-                      Scratch* sc, cudaStream_t s)
+                      Scratch* sc, const Plan* plan, cudaStream_t s)
 {
     if (c.k == 3 && !col && tri_enabled()) return tri_launch_slot(slot, Wh, c, pv, s);  // no bitmaps for k = 3
-    if (count_algo() == KC_ALGO_PIVOT) return sct_launch_slot(slot, Wh, c, pv, col, heavy, heavy_words, s);
+    const int algo = plan ? plan->algo[slot] : count_algo();
+    const int parts = plan ? plan->parts[slot] : 0;
+    if (algo == KC_ALGO_PIVOT) return sct_launch_slot(slot, Wh, c, pv, col, heavy, heavy_words, s);
     if (pv) {
         if (col) return KC_ENOTSUP;
-        return launch_slot_dfs<true, false>(slot, Wh, c, heavy, heavy_words, sc, s);
+        return launch_slot_dfs<true, false>(slot, Wh, c, heavy, heavy_words, sc, parts, s);
     }
-    if (col) return launch_slot_dfs<false, true>(slot, Wh, c, heavy, heavy_words, sc, s);
-    return launch_slot_dfs<false, false>(slot, Wh, c, heavy, heavy_words, sc, s);
+    if (col) return launch_slot_dfs<false, true>(slot, Wh, c, heavy, heavy_words, sc, parts, s);
+    return launch_slot_dfs<false, false>(slot, Wh, c, heavy, heavy_words, sc, parts, s);
 }
 
 Ctx base_ctx(const CountArgs& a)
@@ -550,11 +554,11 @@ void class_range(const kc_graph* g, int k, int slot, int64_t* q0, int64_t* q1)
     if (*q1 < *q0) *q1 = *q0;
 }
 
-int64_t heavy_scratch_words_w(int W, int k, int64_t nheavy, int64_t* slot_words)
+int64_t heavy_scratch_words_w(int W, int k, int64_t nheavy, int64_t* slot_words, int algo)
 {
     *slot_words = 0;
     if (nheavy <= 0) return 0;
-    if (count_algo() == KC_ALGO_PIVOT) {
+    if ((algo < 0 ? count_algo() : algo) == KC_ALGO_PIVOT) {
         *slot_words = sct_heavy_words_w(W, k, 1);
         return sct_heavy_words_w(W, k, nheavy);
     }
@@ -565,23 +569,37 @@ int64_t heavy_scratch_words_w(int W, int k, int64_t nheavy, int64_t* slot_words)
     return lay.total * slots;
 }
 
-int64_t split_scratch_words(const kc_graph* g, int k)
+int64_t split_scratch_words(const kc_graph* g, int k, const Plan* plan)
 {
-    if (count_algo() != KC_ALGO_DFS || !dfs_reg_supported(k)) return 0;
+    if (!dfs_reg_supported(k)) return 0;
     int64_t words = 0;
     for (int slot = 1; slot < kOwnerSlots - 1; ++slot) {
+        if ((plan ? plan->algo[slot] : count_algo()) != KC_ALGO_DFS) continue;
         int64_t q0 = 0, q1 = 0;
         class_range(g, k, slot, &q0, &q1);
-        words += dfs_tile_words(slot_words(slot), k, q1 - q0);
+        words += dfs_tile_words(slot_words(slot), k, q1 - q0, plan ? plan->parts[slot] : 0);
     }
     return words;
 }
 
-int64_t heavy_scratch_words(const kc_graph* g, int k, int64_t* slot_words)
+int64_t heavy_scratch_words(const kc_graph* g, int k, int64_t* slot_words, const Plan* plan)
 {
     int64_t q0 = 0, q1 = 0;
     class_range(g, k, 0, &q0, &q1);
-    return heavy_scratch_words_w((g->max_dplus + 31) / 32, k, q1 - q0, slot_words);
+    return heavy_scratch_words_w((g->max_dplus + 31) / 32, k, q1 - q0, slot_words, plan ? plan->algo[0] : -1);
+}
+
+bool find_plan(const kc_graph* g, int k, bool pv, Plan* out)
+{
+    for (const kc_tuning& t : g->tunings)
+        if (t.k == k && (t.per_vertex != 0) == pv) {
+            for (int i = 0; i < kOwnerSlots; ++i) {
+                out->algo[i] = t.algo[i];
+                out->parts[i] = t.parts[i];
+            }
+            return true;
+        }
+    return false;
 }
 
 kc_status count_launch(const kc_graph* g, const CountArgs& a, unsigned long long* cursors,
@@ -603,7 +621,7 @@ kc_status count_launch(const kc_graph* g, const CountArgs& a, unsigned long long
         c.qstride = nparts;
         c.nitems = span > part ? (span - part + nparts - 1) / nparts : 0;
         c.cursor = cursors + slot;
-        KC_TRY(launch_slot(slot, Wh, c, a.per_vertex, col, heavy_scratch, heavy_words, a.sc, s));
+        KC_TRY(launch_slot(slot, Wh, c, a.per_vertex, col, heavy_scratch, heavy_words, a.sc, a.plan, s));
     }
     return KC_OK;
 }
@@ -640,7 +658,155 @@ kc_status count_batch_launch(const kc_graph* const* gs, int ng, const CountArgs&
         c.gpre = c.gq0 + ng;
         c.nitems = host_tables[(size_t)(slot * per + ng + ng)];
         c.cursor = cursors + slot;
-        KC_TRY(launch_slot(slot, Wh, c, false, col, heavy_scratch, heavy_words, a.sc, s));
+        KC_TRY(launch_slot(slot, Wh, c, false, col, heavy_scratch, heavy_words, a.sc, a.plan, s));
+    }
+    return KC_OK;
+}
+
+// ---------------------------------------------------------------- autotuner
+
+// For every owner class of the graphs gs: run each candidate plan on the
+// class's first owners (queue order: the heaviest of one graph, or the first
+// graphs' owners of a batch), at most kTuneSample of them, once to warm up
+// and once timed with events on s, and keep the fastest.  The outputs of the
+// sample runs go to scratch and are discarded.
+kc_status tune(const kc_graph* const* gs, int ng, int k, bool pv, cudaStream_t s, kc_tuning* out)
+{
+    constexpr int64_t kTuneSample = 256;
+    std::memset(out, 0, sizeof(*out));
+    out->k = k;
+    out->per_vertex = pv ? 1 : 0;
+    for (int i = 0; i < kOwnerSlots; ++i) {
+        out->algo[i] = KC_ALGO_DFS;
+        out->parts[i] = (i >= 1 && i < kOwnerSlots - 1) ? parts_per_owner(slot_words(i), k) : 1;
+    }
+    if (k <= 3 || ng < 1) return KC_OK;
+    if (pv && ng > 1) return KC_EINVAL;  // per-vertex output exists for single graphs only
+    Scratch sc(s);
+    int32_t nmax = 1;
+    int Wh = 1;
+    int64_t nheavy = 0;
+    for (int i = 0; i < ng; ++i) {
+        nmax = std::max(nmax, gs[i]->n);
+        Wh = std::max(Wh, (gs[i]->max_dplus + 31) / 32);
+        int64_t q0 = 0, q1 = 0;
+        class_range(gs[i], k, 0, &q0, &q1);
+        nheavy += q1 - q0;
+    }
+    unsigned long long* small = nullptr;  // [0..1] total, [2..15] cursors, then 2 words per graph
+    KC_TRY(sc.get(&small, 24 + 2 * (int64_t)ng));
+    unsigned long long *pvr = nullptr, *por = nullptr;
+    if (pv) {
+        KC_TRY(sc.get(&pvr, nmax));
+        KC_TRY(sc.get(&por, nmax));
+    }
+    int64_t sw = 0;
+    const int64_t hs = std::min<int64_t>(nheavy, kTuneSample);
+    const int64_t hw = std::max(heavy_scratch_words_w(Wh, k, hs, &sw, KC_ALGO_DFS),
+                                heavy_scratch_words_w(Wh, k, hs, &sw, KC_ALGO_PIVOT));
+    uint32_t* heavy = nullptr;
+    if (hw > 0) KC_TRY(sc.get(&heavy, hw));
+
+    CountArgs a;
+    a.k = k;
+    a.colours = 0;
+    a.seed = 0;
+    a.per_vertex = pv;
+    a.total = small;
+    a.pv = pvr;
+    a.po = por;
+    a.work = nullptr;
+    Ctx base = base_ctx(a);
+    std::vector<int64_t> host_tables;
+    int64_t* tables = nullptr;
+    cc::GraphDesc* dd = nullptr;
+    const int64_t per = 2LL * ng + 1;
+    if (ng == 1) {
+        base.offp = gs[0]->offp;
+        base.adjp = gs[0]->adjp;
+        base.queue = gs[0]->queue;
+        base.perm = gs[0]->perm;
+    } else {
+        std::vector<cc::GraphDesc> hd((size_t)ng);
+        for (int i = 0; i < ng; ++i) hd[(size_t)i] = {gs[i]->offp, gs[i]->adjp, gs[i]->queue, gs[i]->perm};
+        host_tables.assign((size_t)(per * kOwnerSlots), 0);
+        for (int slot = 0; slot < kOwnerSlots; ++slot) {
+            int64_t* hq0 = host_tables.data() + slot * per;
+            int64_t* hpre = hq0 + ng;
+            for (int i = 0; i < ng; ++i) {
+                int64_t q0 = 0, q1 = 0;
+                class_range(gs[i], k, slot, &q0, &q1);
+                hq0[i] = q0;
+                hpre[i + 1] = hpre[i] + (q1 - q0);
+            }
+        }
+        KC_TRY(sc.get(&dd, ng));
+        KC_TRY(sc.get(&tables, (int64_t)host_tables.size()));
+        KC_CK(cudaMemcpyAsync(dd, hd.data(), hd.size() * sizeof(cc::GraphDesc), cudaMemcpyHostToDevice, s));
+        KC_CK(cudaMemcpyAsync(tables, host_tables.data(), host_tables.size() * sizeof(int64_t),
+                              cudaMemcpyHostToDevice, s));
+        KC_CK(cudaStreamSynchronize(s));
+        base.gd = dd;
+        base.ng = ng;
+        base.total = small + 16;
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    KC_CK(cudaEventCreate(&e0));
+    KC_CK(cudaEventCreate(&e1));
+    struct Ev {
+        cudaEvent_t a, b;
+        ~Ev()
+        {
+            cudaEventDestroy(a);
+            cudaEventDestroy(b);
+        }
+    } ev{e0, e1};
+
+    for (int slot = 0; slot < kOwnerSlots; ++slot) {
+        Ctx c = base;
+        int64_t nitems = 0;
+        if (ng == 1) {
+            class_range(gs[0], k, slot, &c.q0, &c.q1);
+            nitems = c.q1 - c.q0;
+        } else {
+            c.gq0 = tables + slot * per;
+            c.gpre = c.gq0 + ng;
+            nitems = host_tables[(size_t)(slot * per + ng + ng)];
+        }
+        if (nitems <= 0) continue;
+        c.nitems = std::min(nitems, kTuneSample);
+        c.cursor = small + 2 + slot;  // slot's cursor and (+ kOwnerSlots) its search cursor
+        const int W = slot_words(slot);
+        std::vector<std::pair<int, int>> cand;  // (algo, parts)
+        cand.push_back({KC_ALGO_DFS, 1});
+        if (slot >= 1 && slot < kOwnerSlots - 1 && W >= 4 && k >= 5 && dfs_reg_supported(k)) {
+            cand.push_back({KC_ALGO_DFS, 4});
+            cand.push_back({KC_ALGO_DFS, 16});
+        }
+        cand.push_back({KC_ALGO_PIVOT, 1});
+        float best = -1.0f;
+        for (const auto& cd : cand) {
+            Plan pl;
+            for (int i = 0; i < kOwnerSlots; ++i) {
+                pl.algo[i] = cd.first;
+                pl.parts[i] = cd.second;
+            }
+            float ms = 0.0f;
+            for (int rep = 0; rep < 2; ++rep) {
+                KC_CK(cudaMemsetAsync(small, 0, (24 + 2 * (size_t)ng) * sizeof(unsigned long long), s));
+                KC_CK(cudaEventRecord(e0, s));
+                KC_TRY(launch_slot(slot, Wh, c, pv, false, heavy, hw, &sc, &pl, s));
+                KC_CK(cudaEventRecord(e1, s));
+                KC_CK(cudaEventSynchronize(e1));
+                KC_CK(cudaEventElapsedTime(&ms, e0, e1));
+            }
+            if (best < 0.0f || ms < best) {
+                best = ms;
+                out->algo[slot] = cd.first;
+                out->parts[slot] = cd.second;
+                out->ms[slot] = ms;
+            }
+        }
     }
     return KC_OK;
 }

@@ -829,9 +829,9 @@ int parts_per_owner(int W, int k)
 
 // Tile memory (32-bit words) a class of width W with `items` owners needs for
 // the split search at k (0: no split).
-int64_t dfs_tile_words(int W, int k, int64_t items)
+int64_t dfs_tile_words(int W, int k, int64_t items, int parts)
 {
-    if (parts_per_owner(W, k) <= 1 || items <= 0) return 0;
+    if ((parts > 0 ? parts : parts_per_owner(W, k)) <= 1 || items <= 0) return 0;
     const int WM = W <= 16 ? W : 0;
     const int64_t per = 32LL * W * row_stride(W, WM);
     return per * items + (items + 3);  // tiles, then the task counters
@@ -841,10 +841,10 @@ int64_t dfs_tile_words(int W, int k, int64_t items)
 // With an allocator and R > 1 the owners' rows are built once into global
 // tiles (k_tile_build) and the R parts copy them; without one (the
 // allocation-free entry point) every owner is searched by one CTA.
-kc_status dfs_reg_launch(const cc::Ctx& c, int W, bool pv, bool col, Scratch* sc, cudaStream_t s)
+kc_status dfs_reg_launch(const cc::Ctx& c, int W, bool pv, bool col, Scratch* sc, int parts, cudaStream_t s)
 {
     const int sms = num_sms();
-    int R = parts_per_owner(W, c.k);
+    int R = parts > 0 ? parts : parts_per_owner(W, c.k);
     if (!sc) R = 1;
     const int NW = W <= 4 ? 4 : 8;
     const int WM = W <= 16 ? W : 0;  // widest class keeps the generic last level
@@ -855,7 +855,7 @@ kc_status dfs_reg_launch(const cc::Ctx& c, int W, bool pv, bool col, Scratch* sc
     unsigned int* ctr = nullptr;
     const int64_t tile_words = 32LL * W * RS;
     if (R > 1) {
-        KC_TRY(sc->get(&tiles, dfs_tile_words(W, c.k, c.nitems)));
+        KC_TRY(sc->get(&tiles, dfs_tile_words(W, c.k, c.nitems, R)));
         ctr = tiles + tile_words * c.nitems;
         KC_CK(cudaMemsetAsync(ctr, 0, (size_t)c.nitems * sizeof(unsigned int), s));
     }

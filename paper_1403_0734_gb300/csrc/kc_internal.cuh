@@ -97,11 +97,18 @@ struct kc_graph {
     mutable kc_status ready_status = KC_OK;
     int64_t ge_small[34] = {};          // #{u : d+(u) >= t}, t = 0..33
     int64_t ge_cls[7] = {};             // #{u : d+(u) >= 32*2^i + 1}, i = 0..5; [6] = 0
+    std::vector<kc_tuning> tunings;     // attached plans (kc_set_tuning), one per (k, per_vertex)
 };
 
 namespace kc {
 
 // ------------------------------------------------------------ counting
+
+// Per-class launch plan of one count (from a kc_tuning); null: the knobs.
+struct Plan {
+    int algo[kOwnerSlots];
+    int parts[kOwnerSlots];
+};
 
 struct CountArgs {
     int k;
@@ -116,6 +123,7 @@ struct CountArgs {
     unsigned long long* work;   // [1] bitmap word-operations executed, nullable
     int part = 0, nparts = 1;   // count only owners at queue positions = part (mod nparts)
     struct Scratch* sc = nullptr;  // allocator for the split search's tiles (null: no split)
+    const Plan* plan = nullptr;    // per-class counter and parts (null: process-wide knobs)
 };
 
 // cursors: kCursorWords zeroed counters.
@@ -133,7 +141,7 @@ kc_status count_batch_launch(const kc_graph* const* gs, int ng, const CountArgs&
 // Queue range of owner slot `slot` for k under the current knobs.
 void class_range(const kc_graph* g, int k, int slot, int64_t* q0, int64_t* q1);
 int slot_words(int slot);
-int64_t heavy_scratch_words_w(int W, int k, int64_t nheavy, int64_t* slot_words);
+int64_t heavy_scratch_words_w(int W, int k, int64_t nheavy, int64_t* slot_words, int algo = -1);
 
 extern bool g_work_enabled;
 extern unsigned long long g_last_work;
@@ -210,10 +218,16 @@ struct DeviceGuard {
 
 // Words of global scratch the heavy (global-bitmap) class needs for k under
 // the current settings; *slot_words receives the size of one tile slot.
-int64_t heavy_scratch_words(const kc_graph* g, int k, int64_t* slot_words);
+int64_t heavy_scratch_words(const kc_graph* g, int k, int64_t* slot_words, const Plan* plan = nullptr);
 
 // Words of global tiles the split search of the shared-memory classes needs
 // for k (allocated by the count from its Scratch).
-int64_t split_scratch_words(const kc_graph* g, int k);
+int64_t split_scratch_words(const kc_graph* g, int k, const Plan* plan = nullptr);
+
+// The plan attached to g for (k, per-vertex output), if any.
+bool find_plan(const kc_graph* g, int k, bool pv, Plan* out);
+
+// Autotuner (count.cu).
+kc_status tune(const kc_graph* const* gs, int ng, int k, bool pv, cudaStream_t s, kc_tuning* out);
 
 }  // namespace kc

@@ -316,11 +316,14 @@ kc_status list_run(const kc_graph* g, int k, unsigned flags, int32_t* buf, int64
         unsigned long long* po = nullptr;
         KC_TRY(sc.get(&po, n));
         KC_CK(cudaMemsetAsync(po, 0, (size_t)n * sizeof(unsigned long long), s));
+        Plan plan;
+        const bool planned = find_plan(g, k, false, &plan);
         int64_t slot_words = 0;
-        const int64_t hw = heavy_scratch_words(g, k, &slot_words);
+        const int64_t hw = heavy_scratch_words(g, k, &slot_words, planned ? &plan : nullptr);
         uint32_t* heavy = nullptr;
         if (hw > 0) KC_TRY(sc.get(&heavy, hw));
         CountArgs a;
+        a.plan = planned ? &plan : nullptr;
         a.k = k;
         a.colours = 0;
         a.seed = 0;

@@ -29,6 +29,8 @@ KC_PARAM_COMPACT_HI = 6
 KC_PARAM_TRI = 7
 KC_ALGO_PIVOT = 0
 KC_ALGO_DFS = 1
+KC_TUNE_PER_VERTEX = 0x10
+CLASS_NAMES = ("global", "w32", "w16", "w8", "w4", "w2", "w1")  # owner classes, launch order
 
 _P = ctypes.c_void_p
 _lib = None
@@ -47,6 +49,11 @@ class KcError(RuntimeError):
 class _Info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("m", ctypes.c_int64), ("max_dplus", ctypes.c_int32),
                 ("wedges", ctypes.c_int64), ("device_bytes", ctypes.c_int64)]
+
+
+class _Tuning(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int32), ("per_vertex", ctypes.c_int32), ("algo", ctypes.c_int32 * 7),
+                ("parts", ctypes.c_int32 * 7), ("ms", ctypes.c_float * 7)]
 
 
 def _load():
@@ -97,6 +104,10 @@ def _load():
     lib.kc_count_batch.restype = st
     lib.kc_count_static.argtypes = [_P, ctypes.c_int, ctypes.c_uint, _P, _P]
     lib.kc_count_static.restype = st
+    lib.kc_tune.argtypes = [_P, ctypes.c_int, ctypes.c_int, ctypes.c_uint, _P, ctypes.POINTER(_Tuning)]
+    lib.kc_tune.restype = st
+    lib.kc_set_tuning.argtypes = [_P, ctypes.POINTER(_Tuning)]
+    lib.kc_set_tuning.restype = st
     lib.kc_set_param.argtypes = [ctypes.c_int, ctypes.c_int64]
     lib.kc_set_param.restype = st
     lib.kc_get_param.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int64)]
@@ -380,3 +391,61 @@ def count_static(g: Graph, k: int, stream=None) -> int:
     _check(_load().kc_count_static(g.handle, k, 0, ctypes.byref(tot), _stream_handle(stream)),
            f"kc_count_static(k={k})")
     return int(tot.value)
+
+
+# ------------------------------------------------------------------ tuning
+
+def tune(graphs, k: int, per_vertex: bool = False, stream=None) -> dict:
+    """Measure the per-class plan (counter and parts per owner) for k on one
+    graph or a batch (kc_tune); returns it as a dict (apply with set_tuning)."""
+    gl = graphs if isinstance(graphs, (list, tuple)) else [graphs]
+    hs = (_P * len(gl))(*[g.handle for g in gl])
+    t = _Tuning()
+    _check(_load().kc_tune(hs, len(gl), k, KC_TUNE_PER_VERTEX if per_vertex else 0, _stream_handle(stream),
+                           ctypes.byref(t)), f"kc_tune(k={k})")
+    return {"k": int(t.k), "per_vertex": bool(t.per_vertex), "algo": [int(x) for x in t.algo],
+            "parts": [int(x) for x in t.parts], "ms": [float(x) for x in t.ms]}
+
+
+def set_tuning(g: Graph, plan: dict | None):
+    """Attach a plan (from tune() or a cache) to g; None removes all plans."""
+    if plan is None:
+        _check(_load().kc_set_tuning(g.handle, None), "kc_set_tuning")
+        return
+    t = _Tuning(int(plan["k"]), int(bool(plan["per_vertex"])), (ctypes.c_int32 * 7)(*plan["algo"]),
+                (ctypes.c_int32 * 7)(*plan["parts"]), (ctypes.c_float * 7)(*plan.get("ms", [0.0] * 7)))
+    _check(_load().kc_set_tuning(g.handle, ctypes.byref(t)), "kc_set_tuning")
+
+
+class TuningCache:
+    """Plans cached in a JSON file, keyed by the graph's statistics (n, m,
+    max |Gamma+|, wedges), k and the output mode, so a graph seen before (or
+    one with the same statistics) is not measured again."""
+
+    def __init__(self, path: str):
+        import json
+        self.path = path
+        try:
+            with open(path) as f:
+                self.plans = json.load(f)
+        except (OSError, ValueError):
+            self.plans = {}
+
+    @staticmethod
+    def key(g: Graph, k: int, per_vertex: bool) -> str:
+        return f"n={g.n},m={g.m},dmax={g.max_dplus},wedges={g.wedges},k={k},pv={int(per_vertex)}"
+
+    def plan(self, g: Graph, k: int, per_vertex: bool = False, stream=None, apply: bool = True) -> dict:
+        import json
+        key = self.key(g, k, per_vertex)
+        p = self.plans.get(key)
+        if p is None:
+            p = tune(g, k, per_vertex, stream)
+            self.plans[key] = p
+            tmp = self.path + ".tmp"
+            with open(tmp, "w") as f:
+                json.dump(self.plans, f, indent=1, sort_keys=True)
+            os.replace(tmp, self.path)
+        if apply:
+            set_tuning(g, p)
+        return p
