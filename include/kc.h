@@ -324,6 +324,27 @@ kc_status kc_set_param(int param, int64_t value);
 kc_status kc_get_param(int param, int64_t* value);
 
 /*
+ * kc_batch -- a batch of graphs prepared once for repeated counts at one k:
+ * the per-class owner tables of kc_count_batch are built and uploaded at
+ * creation, so kc_batch_count only launches kernels on its stream (no host
+ * transfer, no synchronisation) and can be captured into a CUDA graph and
+ * replayed.  The graphs must stay alive (and unchanged) while the batch is.
+ *   kc_batch_create  gs, ng, k as kc_count_batch (k = 3..KC_MAX_K); flags 0;
+ *                    uses the plan attached to gs[0] (kc_set_tuning) at
+ *                    creation; synchronous on `stream`
+ *   kc_batch_count   totals: device array of 2 * ng uint64 words (low, high
+ *                    per graph; high != 0: overflow), overwritten; asynchronous
+ *                    on `stream` (not the legacy default stream when captured)
+ *   kc_batch_free    releases the batch (NULL ignored); no kc_batch_count of
+ *                    it may still be running
+ * Errors: KC_EINVAL, KC_ENOMEM, KC_ECUDA.
+ */
+typedef struct kc_batch kc_batch;
+kc_status kc_batch_create(const kc_graph* const* gs, int ng, int k, unsigned flags, void* stream, kc_batch** out);
+kc_status kc_batch_count(kc_batch* b, uint64_t* totals, void* stream);
+void kc_batch_free(kc_batch* b);
+
+/*
  * Autotuning (batching, owner classes).  The counting kernels take owners in
  * classes by the width of their bitmap row (the queue groups of kc_export):
  *   class 0: |Gamma+| above the shared-memory limit (global-memory tiles),

@@ -441,6 +441,113 @@ kc_status kc_count_batch(const kc_graph* const* gs, int ng, int k, unsigned flag
     return st;
 }
 
+}  // extern "C"
+
+struct kc_batch {
+    int device = 0;
+    int ng = 0;
+    int k = 0;
+    std::vector<const kc_graph*> gs;
+    std::vector<int64_t> host_tables;
+    kc::Plan plan;
+    bool planned = false;
+    void* dev = nullptr;  // descriptors, then tables
+    kc::cc::GraphDesc* descs = nullptr;
+    int64_t* tables = nullptr;
+    int64_t heavy_words = 0;
+};
+
+extern "C" {
+
+kc_status kc_batch_create(const kc_graph* const* gs, int ng, int k, unsigned flags, void* stream, kc_batch** out)
+{
+    if (!out) return KC_EINVAL;
+    *out = nullptr;
+    if (!gs || ng < 1 || k < 3 || k > KC_MAX_K || flags != 0) return KC_EINVAL;
+    for (int i = 0; i < ng; ++i)
+        if (!gs[i] || gs[i]->device != gs[0]->device) return KC_EINVAL;
+    kc::DeviceGuard dg(gs[0]->device);
+    for (int i = 0; i < ng; ++i) KC_TRY(kc::ready(gs[i]));
+    cudaStream_t s = (cudaStream_t)stream;
+    kc_batch* b = new (std::nothrow) kc_batch();
+    if (!b) return KC_ENOMEM;
+    b->device = gs[0]->device;
+    b->ng = ng;
+    b->k = k;
+    b->gs.assign(gs, gs + ng);
+    b->planned = kc::find_plan(gs[0], k, false, &b->plan);
+    kc::batch_tables(gs, ng, k, b->host_tables);
+    std::vector<kc::cc::GraphDesc> hd((size_t)ng);
+    int Wh = 1;
+    int64_t nheavy = 0;
+    for (int i = 0; i < ng; ++i) {
+        hd[(size_t)i] = {gs[i]->offp, gs[i]->adjp, gs[i]->queue, gs[i]->perm};
+        Wh = std::max(Wh, (gs[i]->max_dplus + 31) / 32);
+        int64_t q0 = 0, q1 = 0;
+        kc::class_range(gs[i], k, 0, &q0, &q1);
+        nheavy += q1 - q0;
+    }
+    int64_t slot_words = 0;
+    b->heavy_words = kc::heavy_scratch_words_w(Wh, k, nheavy, &slot_words, b->planned ? b->plan.algo[0] : -1);
+    const size_t dbytes = ((hd.size() * sizeof(kc::cc::GraphDesc) + 255) & ~(size_t)255) +
+                          b->host_tables.size() * sizeof(int64_t);
+    kc_status st = kc::pool_alloc(&b->dev, dbytes, s);
+    if (st != KC_OK) {
+        delete b;
+        return st;
+    }
+    b->descs = (kc::cc::GraphDesc*)b->dev;
+    b->tables = (int64_t*)((char*)b->dev + ((hd.size() * sizeof(kc::cc::GraphDesc) + 255) & ~(size_t)255));
+    cudaError_t e = cudaMemcpyAsync(b->descs, hd.data(), hd.size() * sizeof(kc::cc::GraphDesc),
+                                    cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->tables, b->host_tables.data(), b->host_tables.size() * sizeof(int64_t),
+                            cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        kc::set_cuda_error(e, "kc_batch_create");
+        kc_batch_free(b);
+        return KC_ECUDA;
+    }
+    *out = b;
+    return KC_OK;
+}
+
+kc_status kc_batch_count(kc_batch* b, uint64_t* totals, void* stream)
+{
+    if (!b || !totals) return KC_EINVAL;
+    kc::DeviceGuard dg(b->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    kc::Scratch sc(s);
+    unsigned long long* cursors = nullptr;
+    KC_TRY(sc.get(&cursors, 16));
+    KC_CK(cudaMemsetAsync(cursors, 0, 16 * sizeof(unsigned long long), s));
+    KC_CK(cudaMemsetAsync(totals, 0, 2 * (size_t)b->ng * sizeof(uint64_t), s));
+    uint32_t* heavy = nullptr;
+    if (b->heavy_words > 0) KC_TRY(sc.get(&heavy, b->heavy_words));
+    kc::CountArgs a;
+    a.k = b->k;
+    a.colours = 0;
+    a.seed = 0;
+    a.per_vertex = false;
+    a.total = (unsigned long long*)totals;
+    a.pv = nullptr;
+    a.po = nullptr;
+    a.work = nullptr;
+    a.sc = &sc;
+    a.plan = b->planned ? &b->plan : nullptr;
+    return kc::count_batch_run(b->gs.data(), b->ng, a, b->descs, b->tables, b->host_tables, cursors, heavy,
+                               b->heavy_words, s);
+}
+
+void kc_batch_free(kc_batch* b)
+{
+    if (!b) return;
+    kc::DeviceGuard dg(b->device);
+    kc::pool_free(b->dev, 0);
+    delete b;
+}
+
 kc_status kc_tune(const kc_graph* const* gs, int ng, int k, unsigned flags, void* stream, kc_tuning* out)
 {
     if (!gs || ng < 1 || !out || k < 1 || k > KC_MAX_K) return KC_EINVAL;

@@ -626,16 +626,8 @@ kc_status count_launch(const kc_graph* g, const CountArgs& a, unsigned long long
     return KC_OK;
 }
 
-kc_status count_batch_launch(const kc_graph* const* gs, int ng, const CountArgs& a, const void* descs,
-                             int64_t* tables, unsigned long long* cursors, uint32_t* heavy_scratch,
-                             int64_t heavy_words, std::vector<int64_t>& host_tables, cudaStream_t s)
+void batch_tables(const kc_graph* const* gs, int ng, int k, std::vector<int64_t>& host_tables)
 {
-    Ctx base = base_ctx(a);
-    base.gd = (const cc::GraphDesc*)descs;
-    base.ng = ng;
-    const bool col = a.colours >= 2 || a.pair;
-    int Wh = 1;
-    for (int g = 0; g < ng; ++g) Wh = std::max(Wh, (gs[g]->max_dplus + 31) / 32);
     // per slot: gq0[ng] then gpre[ng + 1]
     const int64_t per = 2LL * ng + 1;
     host_tables.assign((size_t)(per * kOwnerSlots), 0);
@@ -645,13 +637,24 @@ kc_status count_batch_launch(const kc_graph* const* gs, int ng, const CountArgs&
         hpre[0] = 0;
         for (int g = 0; g < ng; ++g) {
             int64_t q0 = 0, q1 = 0;
-            class_range(gs[g], a.k, slot, &q0, &q1);
+            class_range(gs[g], k, slot, &q0, &q1);
             hq0[g] = q0;
             hpre[g + 1] = hpre[g] + (q1 - q0);
         }
     }
-    KC_CK(cudaMemcpyAsync(tables, host_tables.data(), host_tables.size() * sizeof(int64_t),
-                          cudaMemcpyHostToDevice, s));
+}
+
+kc_status count_batch_run(const kc_graph* const* gs, int ng, const CountArgs& a, const void* descs,
+                          const int64_t* tables, const std::vector<int64_t>& host_tables, unsigned long long* cursors,
+                          uint32_t* heavy_scratch, int64_t heavy_words, cudaStream_t s)
+{
+    Ctx base = base_ctx(a);
+    base.gd = (const cc::GraphDesc*)descs;
+    base.ng = ng;
+    const bool col = a.colours >= 2 || a.pair;
+    int Wh = 1;
+    for (int g = 0; g < ng; ++g) Wh = std::max(Wh, (gs[g]->max_dplus + 31) / 32);
+    const int64_t per = 2LL * ng + 1;
     for (int slot = 0; slot < kOwnerSlots; ++slot) {
         Ctx c = base;
         c.gq0 = tables + slot * per;
@@ -661,6 +664,16 @@ kc_status count_batch_launch(const kc_graph* const* gs, int ng, const CountArgs&
         KC_TRY(launch_slot(slot, Wh, c, false, col, heavy_scratch, heavy_words, a.sc, a.plan, s));
     }
     return KC_OK;
+}
+
+kc_status count_batch_launch(const kc_graph* const* gs, int ng, const CountArgs& a, const void* descs,
+                             int64_t* tables, unsigned long long* cursors, uint32_t* heavy_scratch,
+                             int64_t heavy_words, std::vector<int64_t>& host_tables, cudaStream_t s)
+{
+    batch_tables(gs, ng, a.k, host_tables);
+    KC_CK(cudaMemcpyAsync(tables, host_tables.data(), host_tables.size() * sizeof(int64_t),
+                          cudaMemcpyHostToDevice, s));
+    return count_batch_run(gs, ng, a, descs, tables, host_tables, cursors, heavy_scratch, heavy_words, s);
 }
 
 // ---------------------------------------------------------------- autotuner

@@ -138,6 +138,13 @@ kc_status count_batch_launch(const kc_graph* const* gs, int ng, const CountArgs&
                              int64_t* tables, unsigned long long* cursors, uint32_t* heavy_scratch,
                              int64_t heavy_words, std::vector<int64_t>& host_tables, cudaStream_t s);
 
+// Per-class tables of a batch (host) and the launches over device copies of
+// them (no host transfer: capturable in a CUDA graph).
+void batch_tables(const kc_graph* const* gs, int ng, int k, std::vector<int64_t>& host_tables);
+kc_status count_batch_run(const kc_graph* const* gs, int ng, const CountArgs& a, const void* descs,
+                          const int64_t* tables, const std::vector<int64_t>& host_tables, unsigned long long* cursors,
+                          uint32_t* heavy_scratch, int64_t heavy_words, cudaStream_t s);
+
 // Queue range of owner slot `slot` for k under the current knobs.
 void class_range(const kc_graph* g, int k, int slot, int64_t* q0, int64_t* q1);
 int slot_words(int slot);

@@ -104,6 +104,12 @@ def _load():
     lib.kc_count_batch.restype = st
     lib.kc_count_static.argtypes = [_P, ctypes.c_int, ctypes.c_uint, _P, _P]
     lib.kc_count_static.restype = st
+    lib.kc_batch_create.argtypes = [_P, ctypes.c_int, ctypes.c_int, ctypes.c_uint, _P, ctypes.POINTER(_P)]
+    lib.kc_batch_create.restype = st
+    lib.kc_batch_count.argtypes = [_P, _P, _P]
+    lib.kc_batch_count.restype = st
+    lib.kc_batch_free.argtypes = [_P]
+    lib.kc_batch_free.restype = None
     lib.kc_tune.argtypes = [_P, ctypes.c_int, ctypes.c_int, ctypes.c_uint, _P, ctypes.POINTER(_Tuning)]
     lib.kc_tune.restype = st
     lib.kc_set_tuning.argtypes = [_P, ctypes.POINTER(_Tuning)]
@@ -449,3 +455,33 @@ class TuningCache:
         if apply:
             set_tuning(g, p)
         return p
+
+
+class Batch:
+    """Graphs prepared once for repeated counts at one k (kc_batch_*): count()
+    only launches kernels on the stream, so it can be captured into a CUDA
+    graph (torch.cuda.graph) and replayed."""
+
+    def __init__(self, graphs, k: int, stream=None):
+        self.graphs = list(graphs)  # kept alive with the batch
+        hs = (_P * len(self.graphs))(*[g.handle for g in self.graphs])
+        h = _P()
+        _check(_load().kc_batch_create(hs, len(self.graphs), k, 0, _stream_handle(stream), ctypes.byref(h)),
+               f"kc_batch_create(k={k})")
+        self._h = h.value
+        self.k = k
+
+    def count(self, totals, stream=None):
+        """Counts into a device tensor of 2 * len(graphs) int64 (lo, hi words)."""
+        _check(_load().kc_batch_count(self._h, _ptr(totals), _stream_handle(stream)), "kc_batch_count")
+
+    def free(self):
+        if self._h:
+            _load().kc_batch_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
