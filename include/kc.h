@@ -256,13 +256,17 @@ kc_status kc_footprint(const kc_graph* g, int k, int per_vertex, int per_owner, 
 
 /*
  * kc_count_part -- the share of kc_count contributed by one part of the
- * owners: owners are split by their position in the work queue (|Gamma+|
- * descending), position i belonging to part i mod nparts, so the parts are
- * balanced.  Every clique is counted by exactly one owner (Sec. 3), so the
+ * owners.  The owners are split into nparts parts by greedy LPT over the work
+ * estimate w(u) = sum over x in Gamma+(u) of |Gamma+(x)|: taken by w(u)
+ * descending (ties in queue order), each owner joins the part with the least
+ * estimated work so far (ties: the lowest part), so the parts are balanced.
+ * The partition is built on the first call for a given nparts (one pass over
+ * the oriented graph and a host sort, synchronous on `stream`) and kept with
+ * the graph.  Every clique is counted by exactly one owner (Sec. 3), so the
  * totals, per-vertex and per-owner arrays of parts 0..nparts-1 add up to
  * kc_count's.  This is how the count is sharded over GPUs (each GPU holds a
- * replica of the oriented graph and counts one part; the partial totals are
- * summed).
+ * replica of the oriented graph and counts one part; the partial totals and
+ * arrays are summed).
  *   k          3..KC_MAX_K
  *   part       0..nparts-1; other arguments as kc_count
  * Errors: as kc_count.

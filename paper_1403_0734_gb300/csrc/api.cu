@@ -244,6 +244,7 @@ void kc_free(kc_graph* g)
         cudaEventDestroy(g->done);
     }
     kc::pool_free(g->block, 0);
+    for (const kc_graph::Parts& p : g->parts) kc::pool_free(p.queue, 0);
     kc::stats_slot_put(g->hstats);
     delete g;
 }

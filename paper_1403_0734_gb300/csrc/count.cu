@@ -25,6 +25,9 @@
 #include <algorithm>
 #include <climits>
 #include <cstring>
+#include <functional>
+#include <mutex>
+#include <queue>
 
 #include "count_common.cuh"
 
@@ -610,19 +613,107 @@ kc_status count_launch(const kc_graph* g, const CountArgs& a, unsigned long long
     base.adjp = g->adjp;
     base.queue = g->queue;
     base.perm = g->perm;
-    const int64_t part = a.nparts > 1 ? a.part : 0, nparts = a.nparts > 1 ? a.nparts : 1;
+    const kc_graph::Parts* parts = nullptr;
+    if (a.nparts > 1) KC_TRY(graph_parts(g, a.nparts, s, &parts));
     const bool col = a.colours >= 2 || a.pair;  // one colour keeps every pair
     const int Wh = (g->max_dplus + 31) / 32;
     for (int slot = 0; slot < kOwnerSlots; ++slot) {
         Ctx c = base;
         class_range(g, a.k, slot, &c.q0, &c.q1);
-        const int64_t span = c.q1 - c.q0;
-        c.qoff = part;
-        c.qstride = nparts;
-        c.nitems = span > part ? (span - part + nparts - 1) / nparts : 0;
+        if (parts) {  // this part's owners of the class: a contiguous run of its own queue
+            const std::vector<int64_t>& pos = parts->pos[(size_t)a.part];
+            const int64_t p0 = std::lower_bound(pos.begin(), pos.end(), c.q0) - pos.begin();
+            const int64_t p1 = std::lower_bound(pos.begin(), pos.end(), c.q1) - pos.begin();
+            c.queue = parts->queue + parts->off[(size_t)a.part];
+            c.q0 = p0;
+            c.q1 = p1;
+        }
+        c.nitems = c.q1 - c.q0;
         c.cursor = cursors + slot;
         KC_TRY(launch_slot(slot, Wh, c, a.per_vertex, col, heavy_scratch, heavy_words, a.sc, a.plan, s));
     }
+    return KC_OK;
+}
+
+namespace {
+
+// w[r] = sum over x in Gamma+(r) of |Gamma+(x)| for every owner r.
+__global__ void k_work_estimate(const int64_t* __restrict__ offp, const int32_t* __restrict__ adjp,
+                                const int32_t* __restrict__ dplus, int32_t n, unsigned long long* __restrict__ w)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = warp; r < n; r += nwarps) {
+        unsigned long long acc = 0;
+        for (int64_t p = offp[r] + lane; p < offp[r + 1]; p += 32) acc += (unsigned long long)dplus[adjp[p]];
+        acc = cc::warp_sum64(acc);
+        if (lane == 0) w[r] = acc;
+    }
+}
+
+}  // namespace
+
+// Greedy LPT: owners taken by work estimate w(u) descending (ties by queue
+// position), each given to the part with the least work so far (ties: the
+// lowest part), so the parts' sums of w(u) differ by at most one owner's.
+kc_status graph_parts(const kc_graph* g, int nparts, cudaStream_t s, const kc_graph::Parts** out)
+{
+    std::lock_guard<std::mutex> lock(g->mu);
+    for (const kc_graph::Parts& p : g->parts)
+        if (p.nparts == nparts) {
+            *out = &p;
+            return KC_OK;
+        }
+    const int32_t n = g->n;
+    std::vector<unsigned long long> w((size_t)std::max(n, 1));
+    std::vector<int32_t> q((size_t)std::max(n, 1));
+    if (n > 0) {
+        Scratch sc(s);
+        unsigned long long* dw = nullptr;
+        KC_TRY(sc.get(&dw, n));
+        k_work_estimate<<<std::min<int64_t>(((int64_t)n + 7) / 8, (int64_t)num_sms() * 16), 256, 0, s>>>(
+            g->offp, g->adjp, g->dplus, n, dw);
+        KC_LAUNCHED();
+        KC_CK(cudaMemcpyAsync(w.data(), dw, (size_t)n * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+        KC_CK(cudaMemcpyAsync(q.data(), g->queue, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        KC_CK(cudaStreamSynchronize(s));
+    }
+    // positions in queue order; their estimates
+    std::vector<int64_t> order((size_t)n);
+    for (int64_t i = 0; i < n; ++i) order[(size_t)i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int64_t x, int64_t y) {
+        return w[(size_t)q[(size_t)x]] > w[(size_t)q[(size_t)y]];
+    });
+    kc_graph::Parts P;
+    P.nparts = nparts;
+    P.pos.assign((size_t)nparts, {});
+    // min-heap of (load, part): the least loaded part, the lowest on ties
+    std::priority_queue<std::pair<unsigned long long, int>, std::vector<std::pair<unsigned long long, int>>,
+                        std::greater<std::pair<unsigned long long, int>>>
+        heap;
+    for (int p = 0; p < nparts; ++p) heap.push({0ull, p});
+    for (int64_t i : order) {
+        auto [load, best] = heap.top();
+        heap.pop();
+        P.pos[(size_t)best].push_back(i);
+        heap.push({load + w[(size_t)q[(size_t)i]] + 1, best});
+    }
+    std::vector<int32_t> hq;
+    hq.reserve((size_t)n);
+    P.off.assign((size_t)nparts, 0);
+    for (int p = 0; p < nparts; ++p) {
+        std::sort(P.pos[(size_t)p].begin(), P.pos[(size_t)p].end());
+        P.off[(size_t)p] = (int64_t)hq.size();
+        for (int64_t i : P.pos[(size_t)p]) hq.push_back(q[(size_t)i]);
+    }
+    void* dq = nullptr;
+    KC_TRY(pool_alloc(&dq, std::max<size_t>(hq.size(), 1) * sizeof(int32_t), s));
+    if (!hq.empty()) KC_CK(cudaMemcpyAsync(dq, hq.data(), hq.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    KC_CK(cudaStreamSynchronize(s));
+    P.queue = (int32_t*)dq;
+    g->parts.push_back(std::move(P));
+    *out = &g->parts.back();
     return KC_OK;
 }
 

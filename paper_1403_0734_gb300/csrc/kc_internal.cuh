@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cstdint>
 #include <cstddef>
+#include <deque>
 #include <mutex>
 #include <vector>
 #include <cuda_runtime.h>
@@ -98,6 +99,14 @@ struct kc_graph {
     int64_t ge_small[34] = {};          // #{u : d+(u) >= t}, t = 0..33
     int64_t ge_cls[7] = {};             // #{u : d+(u) >= 32*2^i + 1}, i = 0..5; [6] = 0
     std::vector<kc_tuning> tunings;     // attached plans (kc_set_tuning), one per (k, per_vertex)
+    // owner partitions for kc_count_part, built on first use per number of parts
+    struct Parts {
+        int nparts = 0;
+        std::vector<std::vector<int64_t>> pos;  // per part: its queue positions, ascending
+        std::vector<int64_t> off;               // per part: start of its owners in `queue`
+        int32_t* queue = nullptr;               // device: every part's owners (ranks), queue order
+    };
+    mutable std::deque<Parts> parts;          // deque: references stay valid as parts are added
 };
 
 namespace kc {
@@ -233,6 +242,9 @@ int64_t split_scratch_words(const kc_graph* g, int k, const Plan* plan = nullptr
 
 // The plan attached to g for (k, per-vertex output), if any.
 bool find_plan(const kc_graph* g, int k, bool pv, Plan* out);
+
+// The LPT partition of g's owners into nparts parts (built once, cached in g).
+kc_status graph_parts(const kc_graph* g, int nparts, cudaStream_t s, const kc_graph::Parts** out);
 
 // Autotuner (count.cu).
 kc_status tune(const kc_graph* const* gs, int ng, int k, bool pv, cudaStream_t s, kc_tuning* out);

@@ -280,6 +280,13 @@ def count_part(g: Graph, k: int, part: int, nparts: int, per_vertex: bool = Fals
     return int(tot.value), (pv[: g.n] if pv is not None else None), (po[: g.n] if po is not None else None)
 
 
+def count_part_device(g: Graph, k: int, part: int, nparts: int, total, per_vertex=None, per_owner=None,
+                      stream=None):
+    """Asynchronous kc_count_part into device tensors (as count_device)."""
+    _check(_load().kc_count_part(g.handle, k, part, nparts, KC_DEVICE_PTRS, _ptr(total), _ptr(per_vertex),
+                                 _ptr(per_owner), _stream_handle(stream)), f"kc_count_part(k={k}, {part}/{nparts})")
+
+
 def count_batch(graphs, k: int, stream=None):
     """q_k of every graph in one launch sequence (kc_count_batch)."""
     hs = (_P * max(len(graphs), 1))(*[gr.handle for gr in graphs])
