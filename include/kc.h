@@ -244,6 +244,19 @@ kc_status kc_list(const kc_graph* g, int k, unsigned flags, int32_t* buf, int64_
                   kc_list_fn fn, void* user, uint64_t* listed, void* stream);
 
 /*
+ * kc_round2_bytes -- the input volume of Round 2 for k (Sec. 3; App. B bounds
+ * it): the bytes of the lists a count reads to build every G+(u) of an owner
+ * u with |Gamma+(u)| >= k-1, namely 4 |Gamma+(x)| + 16 (the list and its
+ * offsets) for each x in Gamma+(u), plus 4 |Gamma+(u)| for Gamma+(u) itself:
+ * the sum over those owners of 4 w(u) + 20 |Gamma+(u)|, with
+ * w(u) = sum over x in Gamma+(u) of |Gamma+(x)|.  Computed by one pass over
+ * the oriented graph on `stream` (synchronous).
+ *   bytes  out, host
+ * Errors: KC_EINVAL, KC_ENOMEM, KC_ECUDA.
+ */
+kc_status kc_round2_bytes(const kc_graph* g, int k, uint64_t* bytes, void* stream);
+
+/*
  * kc_footprint -- device memory a kc_count / kc_estimate call on g for k
  * allocates (stream-ordered) while it runs, for admission control.
  *   per_vertex, per_owner  nonzero if those outputs are requested

@@ -355,6 +355,14 @@ kc_status kc_footprint(const kc_graph* g, int k, int per_vertex, int per_owner, 
     return KC_OK;
 }
 
+kc_status kc_round2_bytes(const kc_graph* g, int k, uint64_t* bytes, void* stream)
+{
+    if (!g || !bytes || k < 1 || k > KC_MAX_K) return KC_EINVAL;
+    kc::DeviceGuard dg(g->device);
+    KC_TRY(kc::ready(g));
+    return kc::round2_bytes(g, k, bytes, (cudaStream_t)stream);
+}
+
 kc_status kc_count_part(const kc_graph* g, int k, int part, int nparts, unsigned flags, uint64_t* total,
                         uint64_t* per_vertex, uint64_t* per_owner, void* stream)
 {

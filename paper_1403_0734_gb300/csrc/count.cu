@@ -652,7 +652,43 @@ __global__ void k_work_estimate(const int64_t* __restrict__ offp, const int32_t*
     }
 }
 
+// sum over owners with d+ >= dmin of 4 w(u) + 20 d+(u) (Round 2 input bytes)
+__global__ void k_round2_bytes(const int64_t* __restrict__ offp, const int32_t* __restrict__ adjp,
+                               const int32_t* __restrict__ dplus, int32_t n, int dmin,
+                               unsigned long long* __restrict__ out)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long acc = 0;
+    for (int64_t r = warp; r < n; r += nwarps) {
+        const int64_t b = offp[r], e = offp[r + 1];
+        if (e - b < dmin) continue;
+        for (int64_t p = b + lane; p < e; p += 32) acc += 4ull * (unsigned long long)dplus[adjp[p]] + 20ull;
+    }
+    acc = cc::warp_sum64(acc);
+    if (lane == 0 && acc) atomicAdd(out, acc);
+}
+
 }  // namespace
+
+kc_status round2_bytes(const kc_graph* g, int k, uint64_t* bytes, cudaStream_t s)
+{
+    *bytes = 0;
+    if (g->n <= 0 || k < 3) return KC_OK;
+    Scratch sc(s);
+    unsigned long long* d = nullptr;
+    KC_TRY(sc.get(&d, 1));
+    KC_CK(cudaMemsetAsync(d, 0, sizeof(unsigned long long), s));
+    k_round2_bytes<<<std::min<int64_t>(((int64_t)g->n + 7) / 8, (int64_t)num_sms() * 16), 256, 0, s>>>(
+        g->offp, g->adjp, g->dplus, g->n, k - 1, d);
+    KC_LAUNCHED();
+    unsigned long long h = 0;
+    KC_CK(cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, s));
+    KC_CK(cudaStreamSynchronize(s));
+    *bytes = h;
+    return KC_OK;
+}
 
 // Greedy LPT: owners taken by work estimate w(u) descending (ties by queue
 // position), each given to the part with the least work so far (ties: the

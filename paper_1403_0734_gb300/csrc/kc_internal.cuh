@@ -246,6 +246,9 @@ bool find_plan(const kc_graph* g, int k, bool pv, Plan* out);
 // The LPT partition of g's owners into nparts parts (built once, cached in g).
 kc_status graph_parts(const kc_graph* g, int nparts, cudaStream_t s, const kc_graph::Parts** out);
 
+// Round 2 input bytes for k (kc_round2_bytes).
+kc_status round2_bytes(const kc_graph* g, int k, uint64_t* bytes, cudaStream_t s);
+
 // Autotuner (count.cu).
 kc_status tune(const kc_graph* const* gs, int ng, int k, bool pv, cudaStream_t s, kc_tuning* out);
 

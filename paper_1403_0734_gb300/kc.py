@@ -110,6 +110,8 @@ def _load():
     lib.kc_batch_count.restype = st
     lib.kc_batch_free.argtypes = [_P]
     lib.kc_batch_free.restype = None
+    lib.kc_round2_bytes.argtypes = [_P, ctypes.c_int, _P, _P]
+    lib.kc_round2_bytes.restype = st
     lib.kc_tune.argtypes = [_P, ctypes.c_int, ctypes.c_int, ctypes.c_uint, _P, ctypes.POINTER(_Tuning)]
     lib.kc_tune.restype = st
     lib.kc_set_tuning.argtypes = [_P, ctypes.POINTER(_Tuning)]
@@ -257,6 +259,14 @@ def count(g: Graph, k: int, per_vertex: bool = False, per_owner: bool = False, s
     _check(_load().kc_count(g.handle, k, 0, ctypes.byref(tot), _ptr(pv), _ptr(po), _stream_handle(stream)),
            f"kc_count(k={k})")
     return int(tot.value), (pv[: g.n] if pv is not None else None), (po[: g.n] if po is not None else None)
+
+
+def round2_bytes(g: Graph, k: int, stream=None) -> int:
+    """Bytes of Gamma+ lists and offsets a count at k reads to build every
+    G+(u) (kc_round2_bytes): the Round 2 input volume."""
+    b = ctypes.c_uint64(0)
+    _check(_load().kc_round2_bytes(g.handle, k, ctypes.byref(b), _stream_handle(stream)), "kc_round2_bytes")
+    return int(b.value)
 
 
 def footprint(g: Graph, k: int, per_vertex: bool = False, per_owner: bool = False,

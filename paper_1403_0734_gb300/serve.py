@@ -56,6 +56,14 @@ class Result:
     def latency(self) -> float:
         return self.end - self.arrival
 
+    @property
+    def wait(self) -> float:
+        return self.start - self.arrival
+
+    @property
+    def service(self) -> float:
+        return self.end - self.start
+
 
 def poisson_stream(num: int, rate: float, ngraphs: int, seed: int, kmin: int = 3, kmax: int = 6,
                    cmin: int = 2, cmax: int = 16, frac_exact: float = 0.5):
@@ -72,11 +80,56 @@ def poisson_stream(num: int, rate: float, ngraphs: int, seed: int, kmin: int = 3
     return reqs
 
 
+class CostModel:
+    """Online estimate of a request's service time, per request type (graph,
+    k, exact or sampled): the mean of the types' observed times, or before
+    any observation a prior proportional to the graph's edges times a
+    per-k factor learned from all types."""
+
+    def __init__(self, edges):
+        self.edges = list(edges)
+        self.obs: dict = {}
+        self.per_edge: dict = {}
+
+    @staticmethod
+    def _type(req):
+        return (req.graph, req.k, req.colours > 0)
+
+    def estimate(self, req) -> float:
+        o = self.obs.get(self._type(req))
+        if o:
+            return o[0] / o[1]
+        pe = self.per_edge.get(req.k)
+        if pe:
+            return pe[0] / pe[1] * self.edges[req.graph]
+        return 1e-3 * (1 + self.edges[req.graph] / 1e6) * req.k
+
+    def observe(self, req, seconds: float):
+        t = self._type(req)
+        o = self.obs.setdefault(t, [0.0, 0])
+        o[0] += seconds
+        o[1] += 1
+        pe = self.per_edge.setdefault(req.k, [0.0, 0.0])
+        pe[0] += seconds
+        pe[1] += max(1, self.edges[req.graph])
+
+
 class Server:
-    """slots worker streams, FIFO admission under a device-memory budget."""
+    """slots worker streams, admission under a device-memory budget.
+
+    policy "fifo": requests are admitted in arrival order; a request that
+    does not fit the budget holds up the ones behind it.
+    policy "edf": among the arrived requests that fit, the one with the
+    earliest arrival + estimated service time (a CostModel) goes first, so a
+    short request is not stuck behind long ones that arrived just before it,
+    while a long request's turn still comes (its key does not grow)."""
 
     def __init__(self, graphs, slots: int = 4, budget_bytes: int | None = None, backend=None,
-                 footprint=None):
+                 footprint=None, policy: str = "fifo", cost: CostModel | None = None):
+        if policy not in ("fifo", "edf"):
+            raise ValueError("policy is fifo or edf")
+        self.policy = policy
+        self.cost = cost
         self.graphs = graphs
         self.slots = slots
         self.budget = budget_bytes
@@ -117,10 +170,10 @@ class Server:
             with self._cv:
                 while True:
                     if self._queue:
-                        req, fp = self._queue[0]
-                        fits = self.budget is None or self._in_use + fp <= self.budget or self._running == 0
-                        if fits:
-                            self._queue.popleft()
+                        pick = self._pick()
+                        if pick is not None:
+                            req, fp = self._queue[pick]
+                            del self._queue[pick]
                             self._in_use += fp
                             self._running += 1
                             self.max_concurrent = max(self.max_concurrent, self._running)
@@ -136,12 +189,30 @@ class Server:
                 err = f"{type(e).__name__}: {e}"
             finally:
                 end = self._now()
+                if self.cost is not None and err is None:
+                    self.cost.observe(req, end - start)
                 with self._cv:  # the slot, its footprint and the request are always released
                     self._in_use -= fp
                     self._running -= 1
                     self._results.append(Result(req.rid, int(value), float(est), req.arrival, start, end, err))
                     self._done += 1
                     self._cv.notify_all()
+
+    def _fits(self, fp) -> bool:
+        return self.budget is None or self._in_use + fp <= self.budget or self._running == 0
+
+    def _pick(self):
+        """Index in the queue of the request to admit now, or None."""
+        if self.policy == "fifo":
+            return 0 if self._fits(self._queue[0][1]) else None
+        best, key = None, None
+        for i, (req, fp) in enumerate(self._queue):
+            if not self._fits(fp):
+                continue
+            kk = req.arrival + (self.cost.estimate(req) if self.cost else 0.0)
+            if key is None or kk < key:
+                best, key = i, kk
+        return best
 
     def run(self, requests, stream_factory=None, realtime: bool = True, raise_errors: bool = True):
         """Serve `requests` (arrival times relative to the start); returns the
@@ -184,6 +255,14 @@ class Server:
 
 
 def latency_stats(results):
-    lat = np.array([r.latency for r in results]) if results else np.zeros(1)
-    return {"p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
-            "mean_ms": float(lat.mean() * 1e3)}
+    """Latency percentiles, split into queue wait (arrival to start) and
+    service (start to end), so a tail can be told apart: waiting behind other
+    requests, or long requests themselves."""
+    def pct(xs):
+        a = np.array(xs) if xs else np.zeros(1)
+        return float(np.percentile(a, 50) * 1e3), float(np.percentile(a, 99) * 1e3), float(a.mean() * 1e3)
+    p50, p99, mean = pct([r.latency for r in results])
+    w50, w99, wmean = pct([r.wait for r in results])
+    s50, s99, smean = pct([r.service for r in results])
+    return {"p50_ms": p50, "p99_ms": p99, "mean_ms": mean, "wait_p50_ms": w50, "wait_p99_ms": w99,
+            "wait_mean_ms": wmean, "service_p50_ms": s50, "service_p99_ms": s99, "service_mean_ms": smean}

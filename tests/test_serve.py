@@ -119,3 +119,34 @@ def test_failing_request_does_not_hang_the_server(graphs):
     res2, _ = serve.Server(graphs, slots=3, backend=ok, footprint=lambda r: 1).run(
         serve.poisson_stream(10, 0.0, len(graphs), seed=4, kmin=3, kmax=4), realtime=False)
     assert all(r.error is None for r in res2)
+
+
+def test_edf_admission_lets_short_requests_pass(graphs):
+    """A burst of long requests (k = 5, sleep 40 ms) followed by short ones
+    (k = 3, 1 ms) on one slot: FIFO makes every short request wait for all the
+    long ones; EDF (arrival + estimated cost, costs learned per request type)
+    runs them as soon as their cost is known, and every answer is unchanged."""
+    def backend(req, stream):
+        time.sleep(0.04 if req.k == 5 else 0.001)
+        return expected(graphs, req), float(expected(graphs, req))
+
+    reqs = [serve.Request(i, i % len(graphs), 5, 0, i, 0.0) for i in range(6)]
+    reqs += [serve.Request(6 + i, i % len(graphs), 3, 0, 6 + i, 0.001) for i in range(6)]
+    stats = {}
+    for policy in ("fifo", "edf"):
+        cost = serve.CostModel([1000] * len(graphs))
+        # teach the model both request types first (the type means are what EDF uses)
+        cost.observe(reqs[0], 0.04)
+        cost.observe(reqs[6], 0.001)
+        for g in range(len(graphs)):
+            cost.observe(serve.Request(0, g, 5, 0, 0, 0.0), 0.04)
+            cost.observe(serve.Request(0, g, 3, 0, 0, 0.0), 0.001)
+        srv = serve.Server(graphs, slots=1, backend=backend, footprint=lambda r: 1, policy=policy, cost=cost)
+        res, _ = srv.run(reqs, realtime=False)
+        for r, q in zip(res, sorted(reqs, key=lambda x: x.rid)):
+            assert r.value == expected(graphs, q)
+        short = [r for r in res if r.rid >= 6]
+        stats[policy] = max(r.latency for r in short)
+        st = serve.latency_stats(res)
+        assert st["wait_p99_ms"] <= st["p99_ms"] + 1e-6
+    assert stats["edf"] < stats["fifo"] / 2
