@@ -429,10 +429,15 @@ kc_status kc_estimate_csr(const int64_t* off, const int32_t* adj, int32_t n, int
  *              of two uint64 words (low, high)
  * Scratch comes from one 16 MiB __device__ array in the library, held by every
  * GPU that loads it until exit.  The first call on each device looks up the
- * array's device address (make it before any stream capture).  All calls
- * share the array: calls that overlap on the GPU race and must be
- * serialised by the caller.  A graph whose widest owner needs a global tile
- * larger than the array returns KC_ENOTSUP without running.
+ * array's device address, and under lazy module loading (the CUDA default)
+ * that is also when the array's 16 MiB are committed on the device: make one
+ * warm-up call (any graph, k = 3) at start-up, before the caller's memory
+ * manager reserves the device and before any stream capture.  All calls
+ * share the array: calls that overlap on the GPU race and must be serialised
+ * by the caller.  A graph whose widest owner needs a global tile larger than
+ * the array returns KC_ENOTSUP without running (never for exact k = 3 with
+ * the triangle path on, which uses no tiles).  Owners are not split across
+ * CTAs here (the split needs per-call tiles).
  * Errors: as kc_count, plus KC_ENOTSUP.
  */
 kc_status kc_count_static(const kc_graph* g, int k, unsigned flags, uint64_t* total, void* stream);

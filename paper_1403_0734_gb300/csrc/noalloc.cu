@@ -27,8 +27,12 @@
 // Set-up.  The device address of the array is looked up with
 // cudaGetSymbolAddress on the first call on each device (with that device
 // current) and cached; the array's name in host code is only a host-side
-// stand-in and is never passed to a kernel.  Make that first call on a device
-// before any stream capture is started.
+// stand-in and is never passed to a kernel.  Under lazy module loading (the
+// CUDA default) that first call is also when the module holding the array is
+// loaded and its 16 MiB are committed on the device: a caller that must not
+// allocate later makes one warm-up call (any graph, k = 3) at start-up,
+// before its memory manager reserves the device and before any stream
+// capture is started.
 #include <mutex>
 
 #include "kc_internal.cuh"
@@ -43,6 +47,13 @@ static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBy
 
 std::mutex g_mu;
 void* g_dev_ptr[kMaxDevices] = {};
+
+// q_1 or q_2 into the first two words of the static array (low, high).
+__global__ void k_set_total(unsigned long long* t, unsigned long long q)
+{
+    t[0] = q;
+    t[1] = 0ull;
+}
 
 // Device address of g_static_scratch on `dev` (which must be current).
 kc_status scratch_address(int dev, void** out)
@@ -78,27 +89,27 @@ extern "C" kc_status kc_count_static(const kc_graph* g, int k, unsigned flags, u
     } restore{prev, g->device};
     KC_TRY(kc::ready(g));
 
-    if (k <= 2) {  // q_1 = n, q_2 = m: no kernel and no scratch
-        static thread_local unsigned long long tv[2];
-        tv[0] = k == 1 ? (unsigned long long)g->n : (unsigned long long)g->m;
-        tv[1] = 0;
-        if (dev_out) {
-            KC_CK(cudaMemcpyAsync(total, tv, sizeof(tv), cudaMemcpyHostToDevice, s));
-            KC_CK(cudaStreamSynchronize(s));
-        } else {
-            *total = tv[0];
-        }
+    const unsigned long long q12 = k == 1 ? (unsigned long long)g->n : (unsigned long long)g->m;
+    if (k <= 2 && !dev_out) {  // q_1 = n, q_2 = m: nothing runs on the device
+        *total = q12;
         return KC_OK;
     }
 
     void* base = nullptr;
     KC_TRY(scratch_address(g->device, &base));
+    if (k <= 2) {  // device output: written on the stream, asynchronously like every device output
+        k_set_total<<<1, 1, 0, s>>>((unsigned long long*)base, q12);
+        KC_LAUNCHED();
+        KC_CK(cudaMemcpyAsync(total, base, 2 * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+        return KC_OK;
+    }
     unsigned long long* small = (unsigned long long*)base;  // [0..1] total, [2..15] cursors
     uint32_t* tiles = (uint32_t*)((char*)base + kSmallBytes);
     const int64_t tile_words = (int64_t)((kStaticScratchBytes - kSmallBytes) / sizeof(uint32_t));
 
     int64_t per_slot = 0;
-    const int64_t need = kc::heavy_scratch_words(g, k, &per_slot);
+    // exact k = 3 takes the triangle path (no bitmaps, no tiles) when it is on
+    const int64_t need = (k == 3 && kc::tri_enabled()) ? 0 : kc::heavy_scratch_words(g, k, &per_slot);
     int64_t use_words = 0;
     if (need > 0) {
         if (per_slot > tile_words) return KC_ENOTSUP;  // widest owner does not fit the static array
