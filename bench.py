@@ -72,7 +72,7 @@ def parse():
     ap.add_argument("--shard", action="store_true", help="N>1: all ranks count one graph (strong scaling)")
     ap.add_argument("--no-tune", action="store_true", help="count with the library's default knobs")
     ap.add_argument("--no-extras", action="store_true", help="skip the SBM / batched / serving workloads")
-    ap.add_argument("--extras", default="sbm,batch,serving")
+    ap.add_argument("--extras", default="cfff_chunglu,sbm,batch,serving")
     ap.add_argument("--batch-graphs", type=int, default=8192)
     ap.add_argument("--serve-graphs", type=int, default=64)
     # scales 21-22 hold exact k = 6 requests of 30-120 s each on one GB300
@@ -304,6 +304,22 @@ def extra_sbm(kc, graphs, cache):
                     "speedup_vs_exact": dt / float(np.mean(ts))}
         out.append(var)
         G.free()
+    return out
+
+
+def extra_cfff_chunglu(kc, g, plans):
+    """cFFF_k on the benchmark graph: sampled-count time against the exact
+    total-only count for k = 4, 5, 6 and c = 8, 16 (one seed each)."""
+    import torch
+    G = kc.orient(torch.from_numpy(g.off).cuda(), torch.from_numpy(g.adj).cuda())
+    out = {}
+    for k in (4, 5, 6):
+        q, dt = timed(lambda: kc.count(G, k)[0])
+        for c in (8, 16):
+            (s, est, _), de = timed(lambda: kc.estimate(G, k, c, 7))
+            out[f"{k},{c}"] = {"exact_ms": dt * 1e3, "estimate_ms": de * 1e3, "speedup": dt / de,
+                               "rel_err": abs(est - q) / q if q else None}
+    G.free()
     return out
 
 
@@ -601,7 +617,8 @@ def main():
     extra = {}
     if extras:
         extra["generation_s"] = gen_s
-    for name, fn in (("sbm", lambda: extra_sbm(kc, [("sbm_p0.3", gen[1]), ("sbm_dense_p1.0", gen[2])], cache)),
+    for name, fn in (("cfff_chunglu", lambda: extra_cfff_chunglu(kc, g, plans)),
+                     ("sbm", lambda: extra_sbm(kc, [("sbm_p0.3", gen[1]), ("sbm_dense_p1.0", gen[2])], cache)),
                      ("batch", lambda: extra_batch(kc, gen[nb:nbatch_end])),
                      ("serving", lambda: extra_serving(kc, gen[nbatch_end:], scales, args))):
         if name in extras:

@@ -399,8 +399,9 @@ kc_status kc_tune(const kc_graph* const* gs, int ng, int k, unsigned flags, void
 
 /*
  * kc_set_tuning -- attach a plan to g: later exact counts of g (kc_count,
- * kc_count_part, kc_list, kc_count_batch with g as its first graph) for the
- * plan's k and output mode use it.  t = NULL removes every plan of g.
+ * kc_count_part, kc_list, kc_count_batch with g as its first graph) and
+ * colour-sampled estimates (kc_estimate) for the plan's k and output mode
+ * use it.  t = NULL removes every plan of g.
  * Errors: KC_EINVAL (bad k, algorithm or parts).
  */
 kc_status kc_set_tuning(kc_graph* g, const kc_tuning* t);

@@ -118,8 +118,10 @@ kc_status run_count(const kc_graph* g, int k, uint32_t colours, uint64_t seed, u
             KC_TRY(sc.get(&po_rank, n));
             KC_CK(cudaMemsetAsync(po_rank, 0, (size_t)n * sizeof(unsigned long long), s));
         }
+        // the attached plan for k (exact counts; colour-sampled estimates use its
+        // choice of counter per class too -- plain pair sampling keeps the knobs)
         Plan plan;
-        const bool planned = colours == 0 && !pair && find_plan(g, k, per_vertex != nullptr, &plan);
+        const bool planned = !pair && find_plan(g, k, per_vertex != nullptr, &plan);
         int64_t slot_words = 0;
         const int64_t hw = heavy_scratch_words(g, k, &slot_words, planned ? &plan : nullptr);
         uint32_t* heavy = nullptr;

@@ -109,6 +109,7 @@ __global__ void __launch_bounds__(256) k_count_w1(Ctx cb)
         uint32_t col = 0;
         const int32_t ur = COL ? c.perm[r] : 0;
         if (COL && lane < d) col = cc::sample_label(c, ur, c.perm[x]);
+        if (COL) col = cc::class_flag_w1(c, col, d, r0, lane);
 
         // (b) rows: lane j searches x_j in each 32-entry chunk of Gamma+(x_i)
         const uint32_t up = cc::build_rows_w1<COL>(c, x, d, col, ur, lane);
@@ -364,6 +365,7 @@ __global__ void __launch_bounds__(256) k_count_cta(Ctx cb, int W, int levels, ui
         }
         __syncthreads();
         const int Wd = (d + 31) >> 5;  // words in use by this owner
+        if (COL) cc::class_flags_smem<true>(c, sCol, d, r0, threadIdx.x, blockDim.x);
 
         // (b) + (d): rows, split over warps
         cc::build_rows<PV, COL>(c, sL, sCol, d, sA, RS, wid, NW, lane, ur);

@@ -115,6 +115,52 @@ __device__ __forceinline__ bool sample_keep(const Ctx& c, int32_t ur, uint32_t l
     return c.pair ? pair_kept(c.seed, ur, li, lj, c.pthr) : li == lj;
 }
 
+// cFFF_k: a sampled (k-1)-clique of G+(u) lies inside one colour class
+// (Map 2 emits monochromatic pairs only), so a vertex whose class in Gamma+(u)
+// has fewer than k-1 members lies in none, and its Gamma+ list need not be
+// read at all (Round 2 shrinks with the sampling).  Such a vertex's label
+// gets kSkipLabel; the flag is the same for its whole class, so labels still
+// compare equal exactly within a class, and the builders skip its row.
+// Colours are below c <= 2^31 (the flag bit is no colour); plain pair
+// sampling (labels are ids) is not filtered.
+constexpr uint32_t kSkipLabel = 0x80000000u;
+
+__device__ __forceinline__ bool class_filter_on(const Ctx& c) { return !c.pair && c.colours <= kSkipLabel; }
+
+// Lane j holds the label of x_j (j < d): flags small classes (match_any).
+__device__ __forceinline__ uint32_t class_flag_w1(const Ctx& c, uint32_t col, int d, int need, int lane)
+{
+    if (!class_filter_on(c)) return col;
+    const uint32_t key = lane < d ? col : kSkipLabel + (uint32_t)lane;
+    const uint32_t peers = __match_any_sync(kFull, key);
+    return (lane < d && __popc(peers) < need) ? (col | kSkipLabel) : col;
+}
+
+// Labels sCol[0..d) in shared memory, threads t0, t0+nt, ... of the caller
+// (d <= 32 nt): flags small classes.  CTA: every thread of the block calls
+// it (two __syncthreads), else the lanes of one warp (two __syncwarp).
+template <bool CTA>
+__device__ __forceinline__ void class_flags_smem(const Ctx& c, uint32_t* sCol, int d, int need, int t0, int nt)
+{
+    if (!class_filter_on(c)) return;
+    uint32_t small = 0;  // bit q: element t0 + q nt is in a class smaller than need
+    for (int q = 0; q < 32; ++q) {
+        const int j = t0 + q * nt;
+        if (j >= d) break;
+        const uint32_t cj = sCol[j];
+        int cnt = 0;
+        for (int i = 0; i < d && cnt < need; ++i) cnt += sCol[i] == cj;
+        if (cnt < need) small |= 1u << q;
+    }
+    if (CTA) __syncthreads(); else __syncwarp();
+    for (int q = 0; q < 32; ++q) {
+        const int j = t0 + q * nt;
+        if (j >= d) break;
+        if ((small >> q) & 1u) sCol[j] |= kSkipLabel;
+    }
+    if (CTA) __syncthreads(); else __syncwarp();
+}
+
 // 128-bit total as (lo, hi) words.
 __device__ __forceinline__ void add_total(unsigned long long* t, unsigned long long v)
 {
@@ -147,6 +193,7 @@ __device__ __forceinline__ uint32_t build_rows_w1(const Ctx& c, int32_t x, int d
     const int32_t maxL = __shfl_sync(kFull, x, d - 1);
     uint32_t up = 0;
     for (int i = 0; i < d - 1; ++i) {
+        if (COL && (__shfl_sync(kFull, col, i) & kSkipLabel)) continue;  // too small a colour class
         const int32_t xi = __shfl_sync(kFull, x, i);
         const int64_t s0 = c.offp[xi], s1 = c.offp[xi + 1];
         uint32_t row = 0;
@@ -231,9 +278,10 @@ __device__ __forceinline__ void build_rows(const Ctx& c, const int32_t* sL, cons
     const int32_t maxL = sL[d - 1];
     const bool direct = T && T->words > 0;
     for (int i = w0; i < d - 1; i += nw) {
+        const uint32_t ci = COL ? sCol[i] : 0u;
+        if (COL && (ci & kSkipLabel)) continue;  // too small a colour class: no sampled clique
         const int32_t xi = sL[i];
         const int64_t s0 = c.offp[xi], s1 = c.offp[xi + 1];
-        const uint32_t ci = COL ? sCol[i] : 0u;
         for (int64_t p0 = s0; p0 < s1; p0 += 32) {
             const int64_t pp = p0 + lane;
             const int32_t y = pp < s1 ? c.adjp[pp] : INT_MAX;

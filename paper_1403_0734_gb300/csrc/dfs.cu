@@ -632,6 +632,7 @@ __global__ void __launch_bounds__(256, 4) k_dfs_reg(Ctx cb, int W, int R, int cl
         __syncthreads();
         if (!TILE) {
             const int32_t ur = COL ? c.perm[r] : 0;
+            if (COL) cc::class_flags_smem<true>(c, sCol, d, r0, threadIdx.x, blockDim.x);
             cc::SpanTable T{smem + lay.sbits, (uint16_t*)(smem + lay.spre), 0, 0};
             cc::span_table_build(T, sL, d, kSpanWords);
             cc::build_rows<PV, COL>(c, sL, sCol, d, sA, RS, wid, NW, lane, ur, &T);
@@ -802,6 +803,7 @@ __global__ void __launch_bounds__(256) k_tile_build(Ctx cb, int W, uint32_t* til
         }
         for (int64_t j = threadIdx.x; j < (int64_t)d * RS; j += blockDim.x) sA[j] = 0u;
         __syncthreads();
+        if (COL) cc::class_flags_smem<true>(c, sCol, d, cb.k - 1, threadIdx.x, blockDim.x);
         cc::SpanTable T{smem + lay.sbits, (uint16_t*)(smem + lay.spre), 0, 0};
         cc::span_table_build(T, sL, d, kSpanWords);
         cc::build_rows<PV, COL>(c, sL, sCol, d, sA, RS, wid, NW, lane, ur, &T);

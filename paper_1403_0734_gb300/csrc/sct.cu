@@ -75,6 +75,7 @@ __global__ void __launch_bounds__(256) k_sct_w1(Ctx cb)
         uint32_t col = 0;
         const int32_t ur = COL ? c.perm[r] : 0;
         if (COL && lane < d) col = cc::sample_label(c, ur, c.perm[x]);
+        if (COL) col = cc::class_flag_w1(c, col, d, c.k - 1, lane);
         const uint32_t up = cc::build_rows_w1<COL>(c, x, d, col, ur, lane);
         const uint32_t A = up | cc::lower_rows_w1(up, d, lane);  // N(lane) inside G+(u)
 
@@ -258,6 +259,7 @@ __global__ void __launch_bounds__(256) k_sct_warp(Ctx cb, int W, uint32_t* gscra
         for (int64_t j = lane; j < (int64_t)d * RS; j += 32) sA[j] = 0u;
         for (int w = lane; w < Wd; w += 32) cur[w] = w < (d >> 5) ? kFull : ((1u << (d & 31)) - 1u);
         __syncwarp();
+        if (COL) cc::class_flags_smem<false>(c, sCol, d, c.k - 1, lane, 32);
         cc::build_rows<true, COL>(c, sL, sCol, d, sA, RS, 0, 1, lane, ur);
         __syncwarp();
 
