@@ -482,6 +482,113 @@ __device__ unsigned long long compact_count(uint32_t C, int n, int need, const u
     return tot;
 }
 
+// Owners with 33..64 elements (two-word rows), one warp each, without shared
+// memory: lane j holds x_j and x_{j+32} and, as 64-bit words, their rows of
+// G+(u) -- built like the one-word class (each 32-entry chunk of Gamma+(x_i)
+// searched for both elements of every lane by shuffle binary search, four
+// rows' first chunks loaded together) -- then the compact search (cdfs)
+// counts the (k-1)-cliques on those registers.  No block barrier, no
+// per-owner set-up beyond the loads: these owners are too many and too small
+// for a CTA each.
+template <bool PV, bool COL>
+__global__ void __launch_bounds__(256) k_count_w2(Ctx cb)
+{
+    const int lane = threadIdx.x & 31;
+    const int need = cb.k - 1;  // vertices to choose inside G+(u)
+    for (;;) {
+        unsigned long long pos = 0;
+        if (lane == 0) pos = atomicAdd(cb.cursor, 1ull);
+        pos = __shfl_sync(kFull, pos, 0);
+        Ctx c;
+        int32_t r;
+        if (!cc::resolve(cb, (int64_t)pos, c, r)) break;
+        const int64_t b = c.offp[r];
+        const int d = (int)(c.offp[r + 1] - b);  // 33..64
+        const int32_t xa = lane < d ? c.adjp[b + lane] : INT_MAX;
+        const int32_t xb = lane + 32 < d ? c.adjp[b + 32 + lane] : INT_MAX;
+        const int32_t ur = COL ? c.perm[r] : 0;
+        uint32_t cola = 0, colb = 0;
+        if (COL) {
+            if (lane < d) cola = cc::sample_label(c, ur, c.perm[xa]);
+            if (lane + 32 < d) colb = cc::sample_label(c, ur, c.perm[xb]);
+        }
+        const int32_t maxL = __shfl_sync(kFull, xb, (d - 33) & 31);
+        const bool ha = lane < d - 1, hb = lane + 32 < d - 1;
+        const int64_t la0 = ha ? c.offp[xa] : 0, la1 = ha ? c.offp[xa + 1] : 0;
+        const int64_t lb0 = hb ? c.offp[xb] : 0, lb1 = hb ? c.offp[xb + 1] : 0;
+        unsigned long long u0 = 0, u1 = 0;  // upper rows of elements lane, lane + 32
+        for (int i0 = 0; i0 < d - 1; i0 += 4) {
+            int32_t y[4];
+            int64_t s0[4], s1[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const int i = i0 + t;
+                const int64_t a0 = __shfl_sync(kFull, la0, i & 31), a1 = __shfl_sync(kFull, la1, i & 31);
+                const int64_t b0 = __shfl_sync(kFull, lb0, i & 31), b1 = __shfl_sync(kFull, lb1, i & 31);
+                s0[t] = i < 32 ? a0 : b0;
+                s1[t] = i < 32 ? a1 : b1;
+                if (i >= d - 1) s1[t] = s0[t];
+                const int64_t p = s0[t] + lane;
+                y[t] = p < s1[t] ? c.adjp[p] : INT_MAX;
+            }
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const int i = i0 + t;
+                if (i >= d - 1) break;
+                unsigned long long row = 0;
+                for (int64_t p0 = s0[t];;) {
+                    int la = 0, lb = 0;
+#pragma unroll
+                    for (int step = 16; step > 0; step >>= 1) {
+                        const int32_t ya = __shfl_sync(kFull, y[t], la + step - 1);
+                        if (ya < xa) la += step;
+                        const int32_t yb = __shfl_sync(kFull, y[t], lb + step - 1);
+                        if (yb < xb) lb += step;
+                    }
+                    const bool hit_a = __shfl_sync(kFull, y[t], la) == xa && lane > i && lane < d;
+                    const bool hit_b = __shfl_sync(kFull, y[t], lb) == xb && lane + 32 > i && lane + 32 < d;
+                    row |= (unsigned long long)__ballot_sync(kFull, hit_a) |
+                           ((unsigned long long)__ballot_sync(kFull, hit_b) << 32);
+                    p0 += 32;
+                    if (p0 >= s1[t] || __shfl_sync(kFull, y[t], 31) >= maxL) break;
+                    const int64_t p = p0 + lane;
+                    y[t] = p < s1[t] ? c.adjp[p] : INT_MAX;
+                }
+                if (COL) {
+                    const uint32_t ci = i < 32 ? __shfl_sync(kFull, cola, i & 31) : __shfl_sync(kFull, colb, i & 31);
+                    row &= (unsigned long long)__ballot_sync(kFull, cc::sample_keep(c, ur, ci, cola)) |
+                           ((unsigned long long)__ballot_sync(kFull, cc::sample_keep(c, ur, ci, colb)) << 32);
+                }
+                if (lane == (i & 31)) {
+                    if (i < 32) u0 = row; else u1 = row;
+                }
+            }
+        }
+        unsigned long long f0 = u0, f1 = u1;  // full rows (memberships): add the transpose
+        if (PV) {
+            for (int j = 1; j < d; ++j) {
+                const unsigned long long colj = (unsigned long long)__ballot_sync(kFull, (u0 >> j) & 1ull) |
+                                                ((unsigned long long)__ballot_sync(kFull, (u1 >> j) & 1ull) << 32);
+                if (lane == (j & 31)) {
+                    if (j < 32) f0 |= colj; else f1 |= colj;
+                }
+            }
+        }
+        unsigned long long a0 = 0, a1 = 0, wk = 0;
+        const unsigned long long tot = cdfs<PV>(u0, u1, f0, f1, d, need, lane, a0, a1, c.work ? &wk : nullptr);
+        if (lane == 0) {
+            add_total(c.total, tot);
+            if (c.po) c.po[r] = tot;
+            if (PV && tot) atomicAdd(&c.pv[r], tot);
+            if (c.work && wk) atomicAdd(c.work, wk);
+        }
+        if (PV) {
+            if (a0 && lane < d) atomicAdd(&c.pv[xa], a0);
+            if (a1 && lane + 32 < d) atomicAdd(&c.pv[xb], a1);
+        }
+    }
+}
+
 // Chains below a first-level choice: level 0 holds C (elements above i1),
 // need0 >= 3 vertices still to choose.  Returns the cliques completed and
 // credits chain members with their sub-tree totals (per-vertex mode).
@@ -818,6 +925,21 @@ __global__ void __launch_bounds__(256) k_tile_build(Ctx cb, int W, uint32_t* til
 }  // namespace
 
 bool dfs_reg_supported(int k) { return k >= 3 && k - 3 <= kMaxLev; }
+
+// The two-word class (|Gamma+| 33..64), one warp per owner on registers.
+kc_status w2_launch(const cc::Ctx& c, bool pv, bool col, cudaStream_t s)
+{
+    if (c.nitems <= 0) return KC_OK;
+    auto go = [&](auto kern) -> kc_status {
+        const int grid =
+            (int)std::min<int64_t>((c.nitems + 7) / 8, (int64_t)num_sms() * cc::blocks_per_sm(kern, 256, 0));
+        kern<<<grid, 256, 0, s>>>(c);
+        KC_LAUNCHED();
+        return KC_OK;
+    };
+    if (pv) return col ? KC_ENOTSUP : go(k_count_w2<true, false>);
+    return col ? go(k_count_w2<false, true>) : go(k_count_w2<false, false>);
+}
 
 // Parts per owner: heavy owners (rows of 8+ words) are split for k >= 5,
 // where one owner's search can outlast the rest of the class.
