@@ -59,6 +59,7 @@ bool dfs_reg_supported(int k);
 kc_status tri_launch_slot(int slot, int Wh, const cc::Ctx& c, bool pv, cudaStream_t s);
 kc_status dfs_reg_launch(const cc::Ctx& c, int W, bool pv, bool col, Scratch* sc, int parts, cudaStream_t s);
 int64_t dfs_tile_words(int W, int k, int64_t items, int parts);
+kc_status w2_launch(const cc::Ctx& c, bool pv, bool col, cudaStream_t s);
 
 kc_status set_smem_max_words(int64_t v)
 {
@@ -474,6 +475,8 @@ kc_status launch_slot_dfs(int slot, int Wh, const Ctx& c, uint32_t* heavy, int64
         return KC_OK;
     }
     const int W = slot_words(slot);
+    if (W == 2 && parts <= 1 && !(PV && COL) && dfs_reg_supported(k))
+        return w2_launch(c, PV, COL, s);  // a warp per owner, rows in registers
     if (dfs_reg_supported(k)) return dfs_reg_launch(c, W, PV, COL, sc, parts, s);  // register-resident search
     const int NW = warps_for_width(W);
     const Layout lay = make_layout(W, W + 1, NW, levels, PV, COL);
