@@ -46,6 +46,10 @@ sys.path.insert(0, ROOT)
 METRIC = "k-cliques/sec and edges/sec at k=3..7 on 1 GB300; % HBM roofline; batched p50/p99"
 UNIT = "k-cliques/s"
 WORKLOAD = "chung_lu n=1e6 m~2e7 gamma=2.1 wmax=20000, exact k=3..6, per-vertex+per-owner"
+# the headline graph, and a reduced one of the same degree law for profiler
+# captures (its hubs still reach the 16-word class; a k = 6 count takes
+# ~0.3 s instead of ~1.1 s)
+GRAPHS = {"chunglu_1m": (1_000_000, 20_000_000, 2.1, 20000.0), "chunglu_300k": (300_000, 6_000_000, 2.1, 20000.0)}
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "roofline_traffic.json")
 # Word-operation peak of the counting kernels.  A word-op is one 32-bit AND
@@ -69,6 +73,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["kc", "reference"], default="kc")
     ap.add_argument("--ks", default="3,4,5,6")
+    ap.add_argument("--graph", choices=sorted(GRAPHS), default="chunglu_1m",
+                    help="chunglu_300k: reduced graph for profiler captures (not a bench line)")
     ap.add_argument("--shard", action="store_true", help="N>1: all ranks count one graph (strong scaling)")
     ap.add_argument("--no-tune", action="store_true", help="count with the library's default knobs")
     ap.add_argument("--no-extras", action="store_true", help="skip the SBM / batched / serving workloads")
@@ -419,7 +425,7 @@ def main():
 
     # every input, generated before the first CUDA call
     import kcgen
-    specs = [("chung_lu", (1_000_000, 20_000_000, 2.1, 20000.0, 1 if shard else 1 + rank))]
+    specs = [("chung_lu", (*GRAPHS[args.graph], 1 if shard else 1 + rank))]
     if "sbm" in extras:
         specs += [("sbm_2m", (1, 0.3)), ("sbm_2m", (1, 1.0))]
     nb = len(specs)
@@ -543,6 +549,12 @@ def main():
         kc.set_tuning(G, p)
     kc.count(G, kmax, per_vertex=True, per_owner=True)
     work = kc.get_param(kc.KC_PARAM_WORK_COUNT)
+    # the plain ordered search's word-ops (every dense set closed on its
+    # edges): the work the complement count of the timed call avoids
+    kc.set_param(kc.KC_PARAM_COMPLEMENT, 0)
+    kc.count(G, kmax, per_vertex=True, per_owner=True)
+    work_plain = kc.get_param(kc.KC_PARAM_WORK_COUNT)
+    kc.set_param(kc.KC_PARAM_COMPLEMENT, 1)
     kc.set_param(kc.KC_PARAM_WORK_COUNT, 0)
     r2 = {k: kc.round2_bytes(G, k) for k in ks}
     G.free()
@@ -561,7 +573,9 @@ def main():
         pass
     roofline = {"bound": "alu", "kernel": f"kc_count k={kmax} (counting kernels)", "achieved": achieved,
                 "peak": peak_wops, "unit": "Tword-op/s", "frac": achieved / peak_wops, "traffic": traffic,
-                "work_word_ops": work, "peak_kind": f"POPC lanes x SMs x {pk_kind} max SM clock"}
+                "work_word_ops": work, "peak_kind": f"POPC lanes x SMs x {pk_kind} max SM clock",
+                "plain_search_word_ops": work_plain,
+                "effective_frac": work_plain / (kmax_ms * 1e-3) / 1e12 / peak_wops}
     hbm = float(pk.get("hbm_gbs", 6800.0))
     # orientation: HBM-streaming bytes ~ 20m + 32n; its one pass of 2m random
     # L2 gathers bounds it below HBM speed
@@ -637,7 +651,8 @@ def main():
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_all, "higher_is_better": True,
                 "scaling": "strong" if shard else "weak", "vs_baseline": None, "dtype": "u64",
                 "data": "synthetic",
-                "config": {"workload": WORKLOAD + (", seed 1" if shard else ", seed 1+rank"), "n": g.n, "m": g.m,
+                "config": {"workload": (WORKLOAD if args.graph == "chunglu_1m" else WORKLOAD.replace("n=1e6 m~2e7", "n=3e5 m~6e6"))
+                           + (", seed 1" if shard else ", seed 1+rank"), "n": g.n, "m": g.m,
                            "ks": ks, "l2": "flushed between timed steps (512 MiB write)", "parallelism": mode,
                            "counter": "autotuned plans (kc_tune) per k" if plans else args.algo,
                            "orientation_in_step": not shard},

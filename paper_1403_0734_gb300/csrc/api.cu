@@ -600,6 +600,7 @@ kc_status kc_set_param(int param, int64_t value)
     }
     if (param == KC_PARAM_ALGO) return kc::set_count_algo(value);
     if (param == KC_PARAM_TRI) return kc::set_tri(value);
+    if (param == KC_PARAM_COMPLEMENT) return kc::set_complement(value);
     if (param == KC_PARAM_COMPACT_LO) return kc::set_compact_window(value, kc::compact_hi());
     if (param == KC_PARAM_COMPACT_HI) return kc::set_compact_window(kc::compact_lo(), value);
     if (param == KC_PARAM_WORK_COUNT) {
@@ -627,6 +628,10 @@ kc_status kc_get_param(int param, int64_t* value)
     }
     if (param == KC_PARAM_TRI) {
         *value = kc::tri_enabled();
+        return KC_OK;
+    }
+    if (param == KC_PARAM_COMPLEMENT) {
+        *value = kc::complement_enabled();
         return KC_OK;
     }
     if (param == KC_PARAM_COMPACT_LO) {

@@ -57,6 +57,15 @@ kc_status set_compact_window(int64_t lo, int64_t hi)
     return KC_OK;
 }
 
+static int g_complement = 1;
+int complement_enabled() { return g_complement; }
+kc_status set_complement(int64_t v)
+{
+    if (v != 0 && v != 1) return KC_EINVAL;
+    g_complement = (int)v;
+    return KC_OK;
+}
+
 namespace {
 
 struct RLayout {
@@ -237,6 +246,142 @@ __device__ __forceinline__ uint32_t leaf2_any(uint32_t C, int w0, int Wd, const 
     return leaf2_reg<PV>(C, w0, Wd, A, RS, pvlo, pvhi, lane, wk);
 }
 
+// Triangles of a dense G[C] through its complement (per-vertex mode,
+// symmetric rows).  With c = |C|, d_v the degree of v in G[C], nb_v = c-1-d_v,
+// X_v the non-neighbours of v in C (v excluded) and M the non-edges of G[C]:
+// the triangles through v are the edges inside N(v), i.e. C(d_v, 2) less the
+// non-edges inside N(v), and splitting the M non-edges by how they meet v
+// gives  M = nb_v + nonedges(N(v)) + sum_{a in X_v} (nb_a - 1) - nonedges(X_v),
+// so a lane reads its element's row once and then only the rows of the
+// element's few non-neighbours a: nb_a comes from a per-warp byte table (255 =
+// too large for a byte, recounted from the row) and the non-edges inside X_v
+// from popc(X_v & ~row(a)) over the words.
+// A first pass fills the table and sums the degrees (so M); the second runs
+// only if G[C] is dense enough for this to pay (non-edges below a quarter of
+// the edges), else the call returns false and nothing is credited.  C words
+// are read from sC; groups outside [glo, ghi] of C are empty.
+template <int WM>
+__device__ __forceinline__ uint32_t nonadj_words(const uint4* C4, const uint4* F4, int glo, int ghi)
+{
+    uint32_t na = 0;
+#pragma unroll
+    for (int r = 0; r < WM / 4; ++r) {
+        if (r < glo || r > ghi) continue;
+        const uint4 f = F4[r], c4 = C4[r];
+        na += (uint32_t)(__popc(c4.x & ~f.x) + __popc(c4.y & ~f.y) + __popc(c4.z & ~f.z) + __popc(c4.w & ~f.w));
+    }
+    return na;
+}
+
+template <int WM>
+__device__ bool penult3_co(const uint32_t* sC, uint8_t* nb, int glo, int ghi, uint32_t total, uint32_t pre,
+                           uint32_t excl, uint32_t C, const uint32_t* A, int RS, uint32_t* pvlo, uint32_t* pvhi,
+                           int lane, unsigned long long* wk, unsigned long long* out)
+{
+    const uint4* C4 = (const uint4*)sC;
+    const unsigned ng4 = 4u * (unsigned)(ghi - glo + 1);
+    uint32_t nbl = 0;
+    for (uint32_t base = 0; base < total; base += 32) {
+        const uint32_t j = base + (uint32_t)lane;
+        int w = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            const uint32_t pv_ = __shfl_sync(kFull, pre, w + step - 1);
+            if (pv_ <= j) w += step;
+        }
+        const uint32_t cw = __shfl_sync(kFull, C, w);
+        const uint32_t ex = __shfl_sync(kFull, excl, w);
+        if (j < total) {
+            const int e = w * 32 + (int)__fns(cw, 0, (int)(j - ex) + 1);
+            const uint4* Ae4 = (const uint4*)(A + (int64_t)e * RS);
+            uint32_t dg = 0;
+#pragma unroll
+            for (int q = 0; q < WM / 4; ++q) {
+                if (q < glo || q > ghi) continue;
+                const uint4 a = Ae4[q], c4 = C4[q];
+                dg += (uint32_t)(__popc(c4.x & a.x) + __popc(c4.y & a.y) + __popc(c4.z & a.z) + __popc(c4.w & a.w));
+            }
+            const uint32_t nbe = total - 1u - dg;
+            nb[e] = (uint8_t)min(nbe, 255u);
+            nbl += nbe;
+        }
+    }
+    const uint32_t nbsum = __reduce_add_sync(kFull, nbl);  // 2M
+    if (wk) *wk += (unsigned long long)total * ng4;
+    const uint32_t dsum = total * (total - 1u) - nbsum;   // 2 |E(G[C])|
+    if (4ull * nbsum >= (unsigned long long)dsum) return false;
+    __syncwarp();
+    const long long M = (long long)(nbsum >> 1);
+    unsigned long long tot = 0, wl = 0;
+    for (uint32_t base = 0; base < total; base += 32) {
+        const uint32_t j = base + (uint32_t)lane;
+        int w = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            const uint32_t pv_ = __shfl_sync(kFull, pre, w + step - 1);
+            if (pv_ <= j) w += step;
+        }
+        const uint32_t cw = __shfl_sync(kFull, C, w);
+        const uint32_t ex = __shfl_sync(kFull, excl, w);
+        const bool valid = j < total;
+        const int e = valid ? w * 32 + (int)__fns(cw, 0, (int)(j - ex) + 1) : 0;
+        const uint4* Ae4 = (const uint4*)(A + (int64_t)e * RS);
+        uint32_t X[WM];
+#pragma unroll
+        for (int q = 0; q < WM / 4; ++q) {
+            if (!valid || q < glo || q > ghi) {
+                X[4 * q] = X[4 * q + 1] = X[4 * q + 2] = X[4 * q + 3] = 0u;
+                continue;
+            }
+            const uint4 a = Ae4[q], c4 = C4[q];
+            X[4 * q] = c4.x & ~a.x;
+            X[4 * q + 1] = c4.y & ~a.y;
+            X[4 * q + 2] = c4.z & ~a.z;
+            X[4 * q + 3] = c4.w & ~a.w;
+        }
+        uint32_t nbe = 0;
+#pragma unroll
+        for (int q = 0; q < WM; ++q) {
+            if (q == (e >> 5)) X[q] &= ~(1u << (e & 31));
+            nbe += (uint32_t)__popc(X[q]);
+        }
+        // S1 = sum over a in X_e of (nb_a - 1); E2 = twice the non-edges inside X_e
+        uint32_t S1 = 0, E2 = 0;
+#pragma unroll
+        for (int q = 0; q < WM; ++q) {
+            uint32_t bits = X[q];
+            while (bits) {
+                const int a = q * 32 + __ffs(bits) - 1;
+                bits &= bits - 1u;
+                const uint4* F4 = (const uint4*)(A + (int64_t)a * RS);
+                uint32_t na = nb[a];
+                if (na == 255u) na = nonadj_words<WM>(C4, F4, glo, ghi) - 1u;
+                S1 += na - 1u;
+                uint32_t xa = 0;
+#pragma unroll
+                for (int r = 0; r < WM / 4; ++r) {
+                    if (r < glo || r > ghi) continue;
+                    const uint4 f = F4[r];
+                    xa += (uint32_t)(__popc(X[4 * r] & ~f.x) + __popc(X[4 * r + 1] & ~f.y) +
+                                     __popc(X[4 * r + 2] & ~f.z) + __popc(X[4 * r + 3] & ~f.w));
+                }
+                E2 += xa - 1u;  // X_e minus N(a) holds a itself
+                wl += ng4;
+            }
+        }
+        const uint32_t XE = E2 >> 1;
+        if (valid) {
+            const long long de = (long long)(total - 1u - nbe);
+            const long long te = de * (de - 1) / 2 - (M - (long long)nbe - (long long)S1 + (long long)XE);
+            tot += (unsigned long long)te;
+            if (te) pv_add(pvlo, pvhi, e, (unsigned long long)te);
+        }
+    }
+    if (wk) *wk += warp_sum64(wl) + (unsigned long long)total * ng4;
+    *out = warp_sum64(tot) / 3ull;
+    return true;
+}
+
 // All children of a node whose candidate set C (lane w holds word w) still
 // needs three vertices: the cliques below are the triangles of G[C].  Each
 // lane takes one element e of C and forms Ce = C & N(e) in its own
@@ -252,7 +397,7 @@ __device__ __forceinline__ uint32_t leaf2_any(uint32_t C, int w0, int Wd, const 
 // (16-byte aligned).  The work counter gets the words actually ANDed.
 template <bool PV, int WM>
 __device__ unsigned long long penult3(uint32_t C, int Wd, const uint32_t* A, int RS, uint32_t* pvlo,
-                                      uint32_t* pvhi, uint32_t* sC, int lane, unsigned long long* wk)
+                                      uint32_t* pvhi, uint32_t* sC, uint8_t* nb, int lane, unsigned long long* wk)
 {
     if (lane < WM) sC[lane] = C;
     __syncwarp();
@@ -271,6 +416,14 @@ __device__ unsigned long long penult3(uint32_t C, int Wd, const uint32_t* A, int
     }
     const uint32_t total = __shfl_sync(kFull, pre, 31);
     const uint32_t excl = pre - pc;
+    if (PV && nb) {
+        unsigned long long co = 0;
+        const bool done = penult3_co<WM>(sC, nb, glo, ghi, total, pre, excl, C, A, RS, pvlo, pvhi, lane, wk, &co);
+        if (done) {
+            __syncwarp();
+            return co;
+        }
+    }
     unsigned long long tot = 0, wl = 0;
     for (uint32_t base = 0; base < total; base += 32) {
         const uint32_t j = base + (uint32_t)lane;
@@ -594,8 +747,8 @@ __global__ void __launch_bounds__(256) k_count_w2(Ctx cb)
 // credits chain members with their sub-tree totals (per-vertex mode).
 template <bool PV, int WM>
 __device__ unsigned long long dfs_reg(uint32_t c0, int need0, int Wd, const uint32_t* A, int RS, uint32_t* pvlo,
-                                      uint32_t* pvhi, uint32_t* sC, int lane, unsigned long long* wk, int clo,
-                                      int chi)
+                                      uint32_t* pvhi, uint32_t* sC, uint8_t* nb, int lane, unsigned long long* wk,
+                                      int clo, int chi)
 {
     uint32_t st[kMaxLev];
 #pragma unroll
@@ -627,12 +780,13 @@ __device__ unsigned long long dfs_reg(uint32_t c0, int need0, int Wd, const uint
         if (wk) *wk += (unsigned long long)(Wd - fw);
         const int need = need0 - t - 1;
         if (cnt < need) continue;
-        const bool compact = cnt >= clo && cnt <= chi;
-        if (need == 2 || compact || (WM >= 4 && need == 3)) {
+        const bool tri = WM >= 4 && need == 3;
+        const bool compact = !tri && cnt >= clo && cnt <= chi;
+        if (need == 2 || compact || tri) {
             const unsigned long long E =
                 need == 2 ? (unsigned long long)leaf2_any<PV, WM>(cn, fw, Wd, A, RS, pvlo, pvhi, lane, wk)
                 : compact ? compact_count<PV>(cn, cnt, need, A, RS, pvlo, pvhi, lane, wk)
-                          : penult3<PV, (WM >= 4 ? WM : 4)>(cn, Wd, A, RS, pvlo, pvhi, sC, lane, wk);
+                          : penult3<PV, (WM >= 4 ? WM : 4)>(cn, Wd, A, RS, pvlo, pvhi, sC, nb, lane, wk);
             total += E;
             cur_sub += E;
             if (PV && lane == 0 && E) pv_add(pvlo, pvhi, e, E);
@@ -651,18 +805,19 @@ __device__ unsigned long long dfs_reg(uint32_t c0, int need0, int Wd, const uint
 
 // The sub-tree below a candidate set C (lane w holds word w; cnt elements,
 // the lowest in word fw) when `need` >= 2 vertices are still to be chosen:
-// edges of G[C] (need 2), triangles (need 3), a compact copy (small C), or
-// the register search below (need >= 4).  Credits the members met inside.
+// edges of G[C] (need 2), triangles (need 3; in the 4..16-word classes
+// always on the bitmap rows, whose dense sets the complement count closes in
+// about one pass), a compact copy (small C, need >= 4 there), or the
+// register search below.  Credits the members met inside.
 template <bool PV, int WM>
 __device__ __forceinline__ unsigned long long subtree(uint32_t C, int cnt, int need, int fw, int Wd, const uint32_t* A,
-                                                      int RS, uint32_t* pvlo, uint32_t* pvhi, uint32_t* sC, int lane,
-                                                      unsigned long long* wk, int clo, int chi)
+                                                      int RS, uint32_t* pvlo, uint32_t* pvhi, uint32_t* sC, uint8_t* nb,
+                                                      int lane, unsigned long long* wk, int clo, int chi)
 {
-    const bool compact = cnt >= clo && cnt <= chi;
     if (need == 2) return (unsigned long long)leaf2_any<PV, WM>(C, fw, Wd, A, RS, pvlo, pvhi, lane, wk);
-    if (compact) return compact_count<PV>(C, cnt, need, A, RS, pvlo, pvhi, lane, wk);
-    if (WM >= 4 && need == 3) return penult3<PV, (WM >= 4 ? WM : 4)>(C, Wd, A, RS, pvlo, pvhi, sC, lane, wk);
-    return dfs_reg<PV, WM>(C, need, Wd, A, RS, pvlo, pvhi, sC, lane, wk, clo, chi);
+    if (WM >= 4 && need == 3) return penult3<PV, (WM >= 4 ? WM : 4)>(C, Wd, A, RS, pvlo, pvhi, sC, nb, lane, wk);
+    if (cnt >= clo && cnt <= chi) return compact_count<PV>(C, cnt, need, A, RS, pvlo, pvhi, lane, wk);
+    return dfs_reg<PV, WM>(C, need, Wd, A, RS, pvlo, pvhi, sC, nb, lane, wk, clo, chi);
 }
 
 // Row e of G+(u) above e, one word per lane (lane w: word w).
@@ -687,7 +842,7 @@ __device__ __forceinline__ uint32_t upper_word(const uint32_t* A, int RS, int e,
 //       global tile; every part copies it into shared memory and takes tasks
 //       from the owner's global counter.
 template <bool PV, bool COL, int WM, bool TILE>
-__global__ void __launch_bounds__(256, 4) k_dfs_reg(Ctx cb, int W, int R, int clo, int chi, const uint32_t* tiles,
+__global__ void __launch_bounds__(256, 4) k_dfs_reg(Ctx cb, int W, int R, int clo, int chi, int co, const uint32_t* tiles,
                                                   int64_t tile_words, unsigned int* task_ctr)
 {
     extern __shared__ __align__(16) uint32_t smem[];
@@ -702,7 +857,11 @@ __global__ void __launch_bounds__(256, 4) k_dfs_reg(Ctx cb, int W, int R, int cl
     // task prefix over first-level vertices (k >= 6): aliases the span table,
     // which is only used while the rows are built
     unsigned int* sP = smem + lay.sbits;
+    // per-warp byte table of the complement count (classes of 4..16 words:
+    // 8 warps x 32 W bytes fit in the span table after the 512 words of sP)
+    uint8_t* nbw = co ? (uint8_t*)(smem + lay.sbits + 512) + wid * 32 * W : nullptr;
     __shared__ __align__(16) uint32_t s_c[8][32];  // per-warp candidate-set buffer
+    __shared__ unsigned int s_ntask;
     __shared__ unsigned int s_next;
     __shared__ unsigned long long s_tot, s_wk;
     __shared__ long long s_item;
@@ -782,10 +941,10 @@ __global__ void __launch_bounds__(256, 4) k_dfs_reg(Ctx cb, int W, int R, int cl
                         run += v;
                     }
                 }
-                if (lane == 31) sP[d] = inc;
+                if (lane == 31) s_ntask = inc;
             }
             __syncthreads();
-            ntasks = sP[d];
+            ntasks = s_ntask;
         }
         unsigned int* ctr = TILE ? task_ctr + oi : &s_next;
 
@@ -854,7 +1013,7 @@ __global__ void __launch_bounds__(256, 4) k_dfs_reg(Ctx cb, int W, int R, int cl
             if (cnt < need) continue;
             const int fw = __ffs(__ballot_sync(kFull, cset != 0u)) - 1;
             const unsigned long long sub =
-                subtree<PV, WM>(cset, cnt, need, fw, Wd, sA, RS, pvlo, pvhi, s_c[wid], lane, wkp, clo, chi);
+                subtree<PV, WM>(cset, cnt, need, fw, Wd, sA, RS, pvlo, pvhi, s_c[wid], nbw, lane, wkp, clo, chi);
             wtot += sub;
             if (PV && lane == 0 && sub) {
                 pv_add(pvlo, pvhi, e1, sub);
@@ -999,7 +1158,7 @@ kc_status dfs_reg_launch(const cc::Ctx& c, int W, bool pv, bool col, Scratch* sc
         KC_CK(cc::allow_smem(kern, smem));
         const int grid =
             (int)std::min<int64_t>(c.nitems * R, (int64_t)sms * cc::blocks_per_sm(kern, NW * 32, smem));
-        kern<<<grid, NW * 32, smem, s>>>(cs, W, R, g_compact_lo, g_compact_hi, tiles, tile_words, ctr);
+        kern<<<grid, NW * 32, smem, s>>>(cs, W, R, g_compact_lo, g_compact_hi, g_complement, tiles, tile_words, ctr);
         KC_LAUNCHED();
         return KC_OK;
     };

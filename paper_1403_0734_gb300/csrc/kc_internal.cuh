@@ -175,6 +175,8 @@ kc_status list_run(const kc_graph* g, int k, unsigned flags, int32_t* buf, int64
                    uint64_t* listed, cudaStream_t s);
 int tri_enabled();
 kc_status set_tri(int64_t v);
+int complement_enabled();
+kc_status set_complement(int64_t v);
 
 // Stream-ordered allocation from the library's memory pool of the current
 // device (a cudaMemPool that keeps freed memory for reuse instead of

@@ -27,6 +27,7 @@ KC_PARAM_ALGO = 4
 KC_PARAM_COMPACT_LO = 5
 KC_PARAM_COMPACT_HI = 6
 KC_PARAM_TRI = 7
+KC_PARAM_COMPLEMENT = 8
 KC_ALGO_PIVOT = 0
 KC_ALGO_DFS = 1
 KC_TUNE_PER_VERTEX = 0x10

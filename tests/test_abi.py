@@ -94,3 +94,10 @@ def test_params(lib):
     kc.set_param(kc.KC_PARAM_TRI, 1)
     with pytest.raises(kc.KcError):
         kc.set_param(kc.KC_PARAM_TRI, 2)
+    assert kc.get_param(kc.KC_PARAM_COMPLEMENT) == 1
+    kc.set_param(kc.KC_PARAM_COMPLEMENT, 0)
+    assert kc.get_param(kc.KC_PARAM_COMPLEMENT) == 0
+    kc.set_param(kc.KC_PARAM_COMPLEMENT, 1)
+    for bad in (-1, 2):
+        with pytest.raises(kc.KcError):
+            kc.set_param(kc.KC_PARAM_COMPLEMENT, bad)

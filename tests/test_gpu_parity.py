@@ -207,6 +207,24 @@ def test_wide_dense_owners_match_oracle(kc):
             check_count(kc, g, G, k)
 
 
+@pytest.mark.parametrize("complement", [1, 0])
+@pytest.mark.parametrize("n,p,k", [(160, 0.86, 5), (150, 0.88, 5), (90, 0.95, 6), (140, 0.78, 5)])
+def test_dense_random_per_vertex(kc, n, p, k, complement):
+    """Dense G(n, p): the candidate sets closed by the last-three-levels
+    count are dense enough (p >= 0.86) for the complement count of
+    per-vertex mode, or just below its switch (p = 0.78, sets at density
+    ~0.78 and below); with the complement count on and off, both ways of
+    closing them are compared with the oracle, element by element."""
+    g = kcgen.random_small(n, p, 3)
+    G = kc.orient(g.off, g.adj)
+    assert G.max_dplus > 64
+    kc.set_param(kc.KC_PARAM_COMPLEMENT, complement)
+    try:
+        check_count(kc, g, G, k)
+    finally:
+        kc.set_param(kc.KC_PARAM_COMPLEMENT, 1)
+
+
 @pytest.mark.parametrize("n,ks", [(31, (3, 5, 8, 31, 32)), (33, (3, 4, 7, 32)), (64, (3, 4, 6)),
                                   (65, (3, 5)), (200, (3, 4, 5, 7)), (520, (3, 4)), (1100, (3, 4)),
                                   (1500, (3,))])
