@@ -58,6 +58,7 @@ kc_status set_compact_window(int64_t lo, int64_t hi)
 }
 
 static int g_complement = 1;
+
 int complement_enabled() { return g_complement; }
 kc_status set_complement(int64_t v)
 {
@@ -73,6 +74,7 @@ struct RLayout {
 };
 
 constexpr int kSpanWords = 1024;  // direct table of the build: spans up to 32768 ranks
+constexpr int kPairChunk = 4;     // (e1, e2) tasks taken per counter update
 
 __host__ __device__ inline RLayout make_rlayout(int W, int RS, bool pv, bool col, int NW = 0)
 {
@@ -339,34 +341,48 @@ __device__ bool penult3_co(const uint32_t* sC, uint8_t* nb, int glo, int ghi, ui
             X[4 * q + 2] = c4.z & ~a.z;
             X[4 * q + 3] = c4.w & ~a.w;
         }
-        uint32_t nbe = 0;
+        // X holds e itself (rows have no loops): nb_e = |X| - 1
+        uint32_t px = 0;
 #pragma unroll
-        for (int q = 0; q < WM; ++q) {
-            if (q == (e >> 5)) X[q] &= ~(1u << (e & 31));
-            nbe += (uint32_t)__popc(X[q]);
-        }
-        // S1 = sum over a in X_e of (nb_a - 1); E2 = twice the non-edges inside X_e
+        for (int q = 0; q < WM; ++q) px += (uint32_t)__popc(X[q]);
+        const uint32_t nbe = valid ? px - 1u : 0u;
+        // S1 = sum over a in X_e of (nb_a - 1); E2 = twice the non-edges inside
+        // X_e.  The groups of X are visited by a runtime loop (the per-element
+        // body is unrolled over the four words of a group only).
         uint32_t S1 = 0, E2 = 0;
+#pragma unroll 1
+        for (int g = glo; g <= ghi; ++g) {
+            uint32_t xg[4] = {X[0], X[1], X[2], X[3]};
 #pragma unroll
-        for (int q = 0; q < WM; ++q) {
-            uint32_t bits = X[q];
-            while (bits) {
-                const int a = q * 32 + __ffs(bits) - 1;
-                bits &= bits - 1u;
-                const uint4* F4 = (const uint4*)(A + (int64_t)a * RS);
-                uint32_t na = nb[a];
-                if (na == 255u) na = nonadj_words<WM>(C4, F4, glo, ghi) - 1u;
-                S1 += na - 1u;
-                uint32_t xa = 0;
-#pragma unroll
-                for (int r = 0; r < WM / 4; ++r) {
-                    if (r < glo || r > ghi) continue;
-                    const uint4 f = F4[r];
-                    xa += (uint32_t)(__popc(X[4 * r] & ~f.x) + __popc(X[4 * r + 1] & ~f.y) +
-                                     __popc(X[4 * r + 2] & ~f.z) + __popc(X[4 * r + 3] & ~f.w));
+            for (int h = 1; h < WM / 4; ++h)
+                if (g == h) {
+                    xg[0] = X[4 * h];
+                    xg[1] = X[4 * h + 1];
+                    xg[2] = X[4 * h + 2];
+                    xg[3] = X[4 * h + 3];
                 }
-                E2 += xa - 1u;  // X_e minus N(a) holds a itself
-                wl += ng4;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                uint32_t bits = xg[i];
+                while (bits) {
+                    const int a = (4 * g + i) * 32 + __ffs(bits) - 1;
+                    bits &= bits - 1u;
+                    if (a == e) continue;
+                    const uint4* F4 = (const uint4*)(A + (int64_t)a * RS);
+                    uint32_t na = nb[a];
+                    if (na == 255u) na = nonadj_words<WM>(C4, F4, glo, ghi) - 1u;
+                    S1 += na - 1u;
+                    uint32_t xa = 0;
+#pragma unroll
+                    for (int r = 0; r < WM / 4; ++r) {
+                        if (r < glo || r > ghi) continue;
+                        const uint4 f = F4[r];
+                        xa += (uint32_t)(__popc(X[4 * r] & ~f.x) + __popc(X[4 * r + 1] & ~f.y) +
+                                         __popc(X[4 * r + 2] & ~f.z) + __popc(X[4 * r + 3] & ~f.w));
+                    }
+                    E2 += xa - 2u;  // X minus N(a) holds a and e
+                    wl += ng4;
+                }
             }
         }
         const uint32_t XE = E2 >> 1;
@@ -950,74 +966,100 @@ __global__ void __launch_bounds__(256, 4) k_dfs_reg(Ctx cb, int W, int R, int cl
 
         unsigned long long wtot = 0, wk = 0;
         unsigned long long* wkp = c.work ? &wk : nullptr;
+        // pair tasks are taken kPairChunk at a time: one counter update per
+        // chunk, and the chunk's later pairs follow row e1 without a search
+        const unsigned int chunk = pairs ? (unsigned int)kPairChunk : 1u;
         for (;;) {
-            unsigned int t = 0;
-            if (lane == 0) t = atomicAdd(ctr, 1u);
-            t = __shfl_sync(kFull, t, 0);
-            if (t >= ntasks) break;
-            if (r0 == 2) {  // k = 3: edges of G+(u) from e1 = t
-                const int e = (int)t;
-                const uint32_t* Ae = sA + (int64_t)e * RS;
-                const int we = e >> 5, be = e & 31;
-                uint32_t up = 0, all = 0;
-                if (lane < Wd) {
-                    const uint32_t v = Ae[lane];
-                    up = lane > we ? (uint32_t)__popc(v) : (lane == we ? (uint32_t)__popc(v & mask_above(be)) : 0u);
-                    all = (uint32_t)__popc(v);
+            unsigned int t0 = 0;
+            if (lane == 0) t0 = atomicAdd(ctr, chunk);
+            t0 = __shfl_sync(kFull, t0, 0);
+            if (t0 >= ntasks) break;
+            const unsigned int tend = min(t0 + chunk, ntasks);
+            int e1 = 0, e2 = -1;
+            uint32_t u1 = 0;
+            for (unsigned int t = t0; t < tend; ++t) {
+                if (r0 == 2) {  // k = 3: edges of G+(u) from e1 = t
+                    const int e = (int)t;
+                    const uint32_t* Ae = sA + (int64_t)e * RS;
+                    const int we = e >> 5, be = e & 31;
+                    uint32_t up = 0, all = 0;
+                    if (lane < Wd) {
+                        const uint32_t v = Ae[lane];
+                        up = lane > we ? (uint32_t)__popc(v)
+                                       : (lane == we ? (uint32_t)__popc(v & mask_above(be)) : 0u);
+                        all = (uint32_t)__popc(v);
+                    }
+                    up = __reduce_add_sync(kFull, up);
+                    wtot += up;
+                    if (PV) {
+                        all = __reduce_add_sync(kFull, all);
+                        if (lane == 0 && all) pv_add(pvlo, pvhi, e, all);
+                    }
+                    if (wkp) wk += (unsigned long long)(PV ? Wd : Wd - we);
+                    continue;
                 }
-                up = __reduce_add_sync(kFull, up);
-                wtot += up;
-                if (PV) {
-                    all = __reduce_add_sync(kFull, all);
-                    if (lane == 0 && all) pv_add(pvlo, pvhi, e, all);
-                }
-                if (wkp) wk += (unsigned long long)(PV ? Wd : Wd - we);
-                continue;
-            }
-            int e1, e2 = -1;
-            uint32_t cset;
-            int need;
-            if (!pairs) {
-                e1 = (int)t;
-                cset = upper_word(sA, RS, e1, Wd, lane);
-                need = r0 - 1;
-                if (wkp) wk += (unsigned long long)(Wd - (e1 >> 5));
-            } else {
-                // e1: the last vertex whose prefix is <= t (binary search in sP)
-                int lo = 0, hi = d;
-                while (hi - lo > 1) {
-                    const int mid = (lo + hi) >> 1;
-                    if (sP[mid] <= t) lo = mid; else hi = mid;
-                }
-                e1 = lo;
-                const unsigned int j = t - sP[e1];
-                // e2: the j-th element of row e1 above e1
-                const uint32_t u1 = upper_word(sA, RS, e1, Wd, lane);
-                const unsigned int pc = (unsigned int)__popc(u1);
-                unsigned int inc = pc;
+                uint32_t cset;
+                int need;
+                if (!pairs) {
+                    e1 = (int)t;
+                    cset = upper_word(sA, RS, e1, Wd, lane);
+                    need = r0 - 1;
+                    if (wkp) wk += (unsigned long long)(Wd - (e1 >> 5));
+                } else {
+                    if (t == t0) {
+                        // e1: the last vertex whose prefix is <= t (binary search in sP)
+                        int lo = 0, hi = d;
+                        while (hi - lo > 1) {
+                            const int mid = (lo + hi) >> 1;
+                            if (sP[mid] <= t) lo = mid; else hi = mid;
+                        }
+                        e1 = lo;
+                        const unsigned int j = t - sP[e1];
+                        // e2: the j-th element of row e1 above e1
+                        u1 = upper_word(sA, RS, e1, Wd, lane);
+                        const unsigned int pc = (unsigned int)__popc(u1);
+                        unsigned int inc = pc;
 #pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const unsigned int x = __shfl_up_sync(kFull, inc, o);
-                    if (lane >= o) inc += x;
+                        for (int o = 1; o < 32; o <<= 1) {
+                            const unsigned int x = __shfl_up_sync(kFull, inc, o);
+                            if (lane >= o) inc += x;
+                        }
+                        const uint32_t hit = __ballot_sync(kFull, inc > j && inc - pc <= j);
+                        const int hw = __ffs(hit) - 1;
+                        const uint32_t hv = __shfl_sync(kFull, u1, hw);
+                        const unsigned int hx = __shfl_sync(kFull, inc - pc, hw);
+                        e2 = hw * 32 + (int)__fns(hv, 0, (int)(j - hx) + 1);
+                    } else {
+                        // the next pair: the next element of row e1 above e2, else
+                        // the first element of the next row with any (pairs are
+                        // numbered row by row, so t < ntasks guarantees one)
+                        const int w2 = e2 >> 5;
+                        uint32_t rest = lane > w2 ? u1 : (lane == w2 ? (u1 & mask_above(e2 & 31)) : 0u);
+                        uint32_t nzm = __ballot_sync(kFull, rest != 0u);
+                        while (nzm == 0u && e1 + 1 < d) {
+                            ++e1;
+                            u1 = upper_word(sA, RS, e1, Wd, lane);
+                            rest = u1;
+                            nzm = __ballot_sync(kFull, rest != 0u);
+                        }
+                        if (nzm == 0u) break;
+                        const int hw = __ffs(nzm) - 1;
+                        e2 = hw * 32 + __ffs(__shfl_sync(kFull, rest, hw)) - 1;
+                    }
+                    cset = u1 & upper_word(sA, RS, e2, Wd, lane);
+                    need = r0 - 2;
+                    if (wkp) wk += (unsigned long long)(2 * (Wd - (e1 >> 5)));
                 }
-                const uint32_t hit = __ballot_sync(kFull, inc > j && inc - pc <= j);
-                const int hw = __ffs(hit) - 1;
-                const uint32_t hv = __shfl_sync(kFull, u1, hw);
-                const unsigned int hx = __shfl_sync(kFull, inc - pc, hw);
-                e2 = hw * 32 + (int)__fns(hv, 0, (int)(j - hx) + 1);
-                cset = u1 & upper_word(sA, RS, e2, Wd, lane);
-                need = r0 - 2;
-                if (wkp) wk += (unsigned long long)(2 * (Wd - (e1 >> 5)));
-            }
-            const int cnt = (int)__reduce_add_sync(kFull, (unsigned)__popc(cset));
-            if (cnt < need) continue;
-            const int fw = __ffs(__ballot_sync(kFull, cset != 0u)) - 1;
-            const unsigned long long sub =
-                subtree<PV, WM>(cset, cnt, need, fw, Wd, sA, RS, pvlo, pvhi, s_c[wid], nbw, lane, wkp, clo, chi);
-            wtot += sub;
-            if (PV && lane == 0 && sub) {
-                pv_add(pvlo, pvhi, e1, sub);
-                if (e2 >= 0) pv_add(pvlo, pvhi, e2, sub);
+                const int cnt = (int)__reduce_add_sync(kFull, (unsigned)__popc(cset));
+                if (cnt < need) continue;
+                const int fw = __ffs(__ballot_sync(kFull, cset != 0u)) - 1;
+                const unsigned long long sub =
+                    subtree<PV, WM>(cset, cnt, need, fw, Wd, sA, RS, pvlo, pvhi, s_c[wid], nbw, lane, wkp, clo, chi);
+                wtot += sub;
+                if (PV && lane == 0 && sub) {
+                    pv_add(pvlo, pvhi, e1, sub);
+                    if (pairs) pv_add(pvlo, pvhi, e2, sub);
+                }
             }
         }
         if (lane == 0 && wtot) atomicAdd(&s_tot, wtot);
