@@ -1069,10 +1069,10 @@ __global__ void __launch_bounds__(256, 4) k_dfs_reg(Ctx cb, int W, int R, int cl
         if (threadIdx.x == 0) {
             add_total(c.total, tot);
             if (c.po && tot) atomicAdd(&c.po[r], tot);  // the R parts add up
-            if (PV && tot) atomicAdd(&c.pv[r], tot);
+            if (PV && c.pv && tot) atomicAdd(&c.pv[r], tot);
             if (c.work && s_wk) atomicAdd(c.work, s_wk);
         }
-        if (PV)
+        if (PV && c.pv)  // (no output array: symmetric rows chosen for speed only)
             for (int j = threadIdx.x; j < d; j += blockDim.x) {
                 const unsigned long long v = ((unsigned long long)pvhi[j] << 32) | pvlo[j];
                 if (v) atomicAdd(&c.pv[sL[j]], v);
@@ -1173,8 +1173,13 @@ kc_status dfs_reg_launch(const cc::Ctx& c, int W, bool pv, bool col, Scratch* sc
     if (!sc) R = 1;
     const int NW = W <= 4 ? 4 : 8;
     const int WM = W <= 16 ? W : 0;  // widest class keeps the generic last level
+    // Totals at k >= 6 in the 4..16-word classes run on symmetric rows too:
+    // their dense need-3 sets then take the complement count, which beats
+    // closing them on upper rows; the memberships stay in shared memory
+    // (c.pv is null) and are dropped.  The layout follows the kernel chosen.
+    const bool sym = pv || (!col && g_complement && c.k >= 6 && WM >= 4);
     const int RS = row_stride(W, WM);
-    const RLayout lay = make_rlayout(W, RS, pv, col, NW);
+    const RLayout lay = make_rlayout(W, RS, sym, col, NW);
     const size_t smem = (size_t)lay.total * 4;
     uint32_t* tiles = nullptr;
     unsigned int* ctr = nullptr;
@@ -1219,7 +1224,7 @@ kc_status dfs_reg_launch(const cc::Ctx& c, int W, bool pv, bool col, Scratch* sc
         }
 #undef KC_DFS_PICK
     };
-    if (pv) return col ? KC_ENOTSUP : by_width(std::true_type{}, std::false_type{});
+    if (sym) return col ? KC_ENOTSUP : by_width(std::true_type{}, std::false_type{});
     return col ? by_width(std::false_type{}, std::true_type{}) : by_width(std::false_type{}, std::false_type{});
 }
 
