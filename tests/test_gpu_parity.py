@@ -225,6 +225,39 @@ def test_dense_random_per_vertex(kc, n, p, k, complement):
         kc.set_param(kc.KC_PARAM_COMPLEMENT, 1)
 
 
+def test_complement_count_with_saturated_non_degrees(kc):
+    """A dense candidate set in which one element has more than 254
+    non-neighbours (its byte in the per-warp non-degree table saturates and
+    the count falls back to its row).  K_500 on core = S + T (|S| = 200,
+    |T| = 300); a vertex a adjacent to S only; 5 pendants on every vertex of
+    T and 400 on a, so that by degree S < T < a.  An owner in S has G+(u) =
+    (S above it) + T + a, 16-word rows, and at k = 5 each of its first-level
+    sets holds a with its 300 non-neighbours T.  Closed forms: q_k =
+    C(500, k) + C(200, k-1); memberships C(200, k-1) for a, C(499, k-1) +
+    C(199, k-2) on S, C(499, k-1) on T, 0 on the pendants."""
+    S, T = np.arange(200), np.arange(200, 500)
+    a = 500
+    core = np.arange(500)
+    iu, ju = np.triu_indices(500, 1)
+    edges = [np.stack([core[iu], core[ju]], axis=1), np.stack([np.full(200, a), S], axis=1)]
+    nxt = 501
+    pend_t = np.stack([np.repeat(T, 5), nxt + np.arange(1500)], axis=1)
+    nxt += 1500
+    pend_a = np.stack([np.full(400, a), nxt + np.arange(400)], axis=1)
+    nxt += 400
+    g = kcgen.from_edges(nxt, np.concatenate(edges + [pend_t, pend_a]), "k500_split_core")
+    G = kc.orient(g.off, g.adj)
+    assert 257 <= G.max_dplus <= 512
+    for k in (4, 5, 6):
+        total, pv, _ = kc.count(G, k, per_vertex=True)
+        assert total == comb(500, k) + comb(200, k - 1), k
+        assert int(pv[a]) == comb(200, k - 1)
+        assert np.all(pv[S] == comb(499, k - 1) + comb(199, k - 2))
+        assert np.all(pv[T] == comb(499, k - 1))
+        assert np.all(pv[501:] == 0)
+        assert kc.count(G, k)[0] == total  # totals on symmetric rows (k = 6) and upper rows
+
+
 @pytest.mark.parametrize("n,ks", [(31, (3, 5, 8, 31, 32)), (33, (3, 4, 7, 32)), (64, (3, 4, 6)),
                                   (65, (3, 5)), (200, (3, 4, 5, 7)), (520, (3, 4)), (1100, (3, 4)),
                                   (1500, (3,))])
