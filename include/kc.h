@@ -326,13 +326,16 @@ kc_status kc_count_batch(const kc_graph* const* gs, int ng, int k, unsigned flag
  *   KC_PARAM_TRI  1 (default): exact k = 3 counts take the triangle path --
  *       each y of Gamma+(x_i) found in Gamma+(u) is counted directly (node
  *       iterator, no G+(u) bitmap); 0: the bitmap path used for larger k.
- *   KC_PARAM_COMPLEMENT  1 (default): in per-vertex mode, the ordered search
- *       of the 4-, 8- and 16-word classes closes a candidate set C that still
- *       needs three vertices through the complement of G[C] when C is dense
- *       (non-edges below a quarter of the edges): the triangles through each
- *       v of C follow from the degrees in G[C] and the rows of v's
- *       non-neighbours, so only the rows of non-neighbours are read; 0: every
- *       such set is closed on its edges (one row read per neighbour).
+ *   KC_PARAM_COMPLEMENT  1 (default): the ordered search of the 4-, 8- and
+ *       16-word classes closes a candidate set C that still needs three
+ *       vertices through the complement of G[C] when C is dense (non-edges
+ *       below a quarter of the edges): the triangles through each v of C
+ *       follow from the degrees in G[C] and the rows of v's non-neighbours,
+ *       so only the rows of non-neighbours are read.  It needs symmetric
+ *       rows: per-vertex counts have them, and totals at k >= 6 in those
+ *       classes take them for this (their memberships are dropped).  0: every
+ *       such set is closed on its edges (one row read per neighbour) and
+ *       totals keep upper-triangular rows.
  * kc_set_param returns KC_EINVAL for an unknown knob or a value out of range.
  */
 #define KC_PARAM_SMEM_MAX_WORDS 1
