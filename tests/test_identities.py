@@ -13,6 +13,10 @@ v number
 the non-edges among them, and every non-edge of G[C] either touches v,
 lies inside N(v), or has an end in X_v.)  The per-clique memberships and the
 total sum_v t_v / 3 of the k-clique count follow from it.
+
+The second identity (4-cliques through each vertex of a dense graph, from
+its sparse complement) is not used by the kernels yet; it is pinned here as
+the basis of the next level of the complement count.
 """
 import itertools
 
@@ -67,3 +71,71 @@ def test_complement_identity_special_cases():
     # empty graph: no triangles
     A = np.zeros((7, 7), dtype=np.int64)
     assert np.all(complement_formula(A) == 0)
+
+
+# --- the next level: 4-cliques through each vertex of a dense graph -------
+#
+# Not used by the kernels yet.  It is the identity a first-level complement
+# count would rest on (k = 6 closed per first-level vertex e1 instead of per
+# pair (e1, e2)).  K_v = sum over edge sets F of the complement with
+# |V(F) + v| = j <= 4 of (-1)^|F| C(c - j, 4 - j).  Grouping F by shape gives
+# terms in n̄ (complement degrees), M (complement edges), cherries,
+# triangles and 3-edge paths of the complement around v, plus, for each
+# 4-set q through v with e_q >= 4 complement edges inside,
+# C(e_q, 4) - C(e_q, 5) + C(e_q, 6).
+
+def k4_through_complement(A):
+    from math import comb
+    n = A.shape[0]
+    B = (~A.astype(bool)) & ~np.eye(n, dtype=bool)
+    X = [np.flatnonzero(B[i]).tolist() for i in range(n)]
+    nb = [len(x) for x in X]
+    M = sum(nb) // 2
+    P = sum(comb(d, 2) for d in nb)  # cherries (2-paths) of the complement
+    tri = np.zeros(n, dtype=np.int64)
+    for a, b, c in itertools.combinations(range(n), 3):
+        if B[a, b] and B[a, c] and B[b, c]:
+            tri[[a, b, c]] += 1
+    T = int(tri.sum()) // 3
+    c = n
+    out = np.zeros(n, dtype=np.int64)
+    for v in range(n):
+        Xv = X[v]
+        s1 = sum(nb[a] - 1 for a in Xv)
+        K = comb(c - 1, 3) - nb[v] * comb(c - 2, 2) - (M - nb[v]) * (c - 3)        # |F| = 0, 1
+        K += (comb(nb[v], 2) + s1) * (c - 3)                                      # |F| = 2 on 3 vertices
+        K += sum(M - nb[v] - nb[a] + 1 for a in Xv) + P - comb(nb[v], 2) - s1     # |F| = 2 on 4 vertices
+        K -= int(tri[v]) * (c - 3) + (T - int(tri[v]))                            # |F| = 3: triangles
+        K -= comb(nb[v], 3) + sum(comb(nb[a] - 1, 2) for a in Xv)                 # |F| = 3: stars
+        for a in Xv:                                                              # |F| = 3: paths
+            for b in X[a]:
+                if b != v:
+                    K -= nb[b] - 1 - int(B[b, v])      # v - a - b - d
+            for b in Xv:
+                if b != a:
+                    K -= nb[b] - 1 - int(B[b, a])      # a - v - b - d
+        for t3 in itertools.combinations([u for u in range(n) if u != v], 3):    # |F| >= 4
+            q = (v,) + t3
+            e = sum(int(B[x, y]) for x, y in itertools.combinations(q, 2))
+            K += comb(e, 4) - comb(e, 5) + comb(e, 6)
+        out[v] = K
+    return out
+
+
+def k4_through_brute(A):
+    n = A.shape[0]
+    K = np.zeros(n, dtype=np.int64)
+    for q in itertools.combinations(range(n), 4):
+        if all(A[x, y] for x, y in itertools.combinations(q, 2)):
+            K[list(q)] += 1
+    return K
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_k4_complement_identity(seed):
+    rng = np.random.default_rng(100 + seed)
+    for n in (4, 7, 11, 15):
+        for p in (0.6, 0.85, 0.95, 1.0):
+            U = np.triu(rng.random((n, n)) < p, 1)
+            A = (U | U.T).astype(np.int64)
+            assert np.array_equal(k4_through_complement(A), k4_through_brute(A)), (seed, n, p)
