@@ -139,3 +139,48 @@ def test_k4_complement_identity(seed):
             U = np.triu(rng.random((n, n)) < p, 1)
             A = (U | U.T).astype(np.int64)
             assert np.array_equal(k4_through_complement(A), k4_through_brute(A)), (seed, n, p)
+
+
+def k4_through_complement_local(A):
+    """The same K_v with the >= 4-edge term as subgraph counts of the
+    complement through v (4-cycles, paws, diamonds, K4s), so that every term
+    comes from per-vertex tables (nb, complement triangles tt, s1) and from
+    pairs inside X_v -- no 4-set enumeration."""
+    from math import comb
+    n = A.shape[0]
+    B = (~A.astype(bool)) & ~np.eye(n, dtype=bool)
+    X = [set(np.flatnonzero(B[i]).tolist()) for i in range(n)]
+    nb = [len(x) for x in X]
+    M = sum(nb) // 2
+    P = sum(comb(d, 2) for d in nb)
+    tt = [sum(1 for a, b in itertools.combinations(sorted(X[w]), 2) if B[a, b]) for w in range(n)]
+    T = sum(tt) // 3
+    s1 = [sum(nb[a] - 1 for a in X[w]) for w in range(n)]
+    c = n
+    out = np.zeros(n, dtype=np.int64)
+    for v in range(n):
+        Xv = sorted(X[v])
+        nv, t = nb[v], tt[v]
+        K = comb(c - 1, 3) - nv * comb(c - 2, 2) - (M - nv) * (c - 3)
+        K += (comb(nv, 2) + s1[v]) * (c - 3)
+        K += nv * (M - nv + 1) - sum(nb[a] for a in Xv) + P - comb(nv, 2) - s1[v]
+        K -= t * (c - 3) + (T - t) + comb(nv, 3) + sum(comb(nb[a] - 1, 2) for a in Xv)
+        K -= sum(s1[a] for a in Xv) - nv * (nv - 1) + (nv - 1) * s1[v] - 4 * t   # 3-edge paths
+        tris = [(a, b) for a, b in itertools.combinations(Xv, 2) if B[a, b]]
+        c4 = sum(len(X[a] & X[b]) - 1 for a, b in itertools.combinations(Xv, 2))
+        paw = (t * (nv - 2) + sum(nb[a] + nb[b] - 4 for a, b in tris)
+               + sum(tt[a] - len(X[a] & X[v]) for a in Xv))
+        dia = sum(comb(len(X[v] & X[a]), 2) for a in Xv) + sum(len(X[a] & X[b]) - 1 for a, b in tris)
+        k4 = sum(len(X[v] & X[a] & X[b]) for a, b in tris) // 3
+        out[v] = K + c4 + paw - dia + k4
+    return out
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_k4_complement_local_form(seed):
+    rng = np.random.default_rng(200 + seed)
+    for n in (4, 8, 13, 17):
+        for p in (0.5, 0.85, 0.95, 1.0):
+            U = np.triu(rng.random((n, n)) < p, 1)
+            A = (U | U.T).astype(np.int64)
+            assert np.array_equal(k4_through_complement_local(A), k4_through_brute(A)), (seed, n, p)
