@@ -184,3 +184,84 @@ def test_k4_complement_local_form(seed):
             U = np.triu(rng.random((n, n)) < p, 1)
             A = (U | U.T).astype(np.int64)
             assert np.array_equal(k4_through_complement_local(A), k4_through_brute(A)), (seed, n, p)
+
+
+def k4_word_level(rows, C):
+    """The first-level complement count as a kernel would run it on bitmap
+    words: X' = C & ~row(v) holds v itself, so every popcount of X' sets is
+    corrected for the elements it holds (the corrections below).  Three
+    passes: non-degrees (M, cherries P); S1 and complement triangles tt per
+    element; then K_v from those tables and two-hop walks in the complement.
+    Returns {v: K_v}, or None when G[C] is not dense (non-edges >= a quarter
+    of the edges)."""
+    from math import comb
+
+    def popc(x):
+        return bin(x).count("1")
+
+    el = [v for v in range(len(rows)) if (C >> v) & 1]
+    c = len(el)
+    Xp = {v: C & ~rows[v] for v in el}
+    nb = {v: c - 1 - popc(C & rows[v]) for v in el}
+    nbsum = sum(nb.values())
+    if 4 * nbsum >= c * (c - 1) - nbsum:
+        return None
+    M, P = nbsum // 2, sum(comb(nb[v], 2) for v in el)
+    s1, tt = {}, {}
+    for v in el:
+        X = [a for a in el if a != v and (Xp[v] >> a) & 1]
+        s1[v] = sum(nb[a] - 1 for a in X)
+        tt[v] = sum(popc(Xp[v] & ~rows[a] & C) - 2 for a in X) // 2   # X' \ N(a) holds a and v
+    T = sum(tt.values()) // 3
+    K = {}
+    for v in el:
+        nv, t = nb[v], tt[v]
+        sums = dict(nb=0, cnb=0, s1=0, tt=0, co=0, nbco=0, cco=0)
+        W1 = W2 = W3 = 0
+        for a in (a for a in el if a != v and (Xp[v] >> a) & 1):
+            co = popc(Xp[v] & Xp[a]) - 2                  # |X_v & X_a|: X' sets hold v and a
+            sums["nb"] += nb[a]; sums["cnb"] += comb(nb[a] - 1, 2); sums["s1"] += s1[a]; sums["tt"] += tt[a]
+            sums["co"] += co; sums["nbco"] += nb[a] * co; sums["cco"] += comb(co, 2)
+            for x in (x for x in el if x != a and (Xp[a] >> x) & 1):
+                if x == v:
+                    coxv, tri3, inv = nv, co, 0
+                else:
+                    inv = (Xp[v] >> x) & 1
+                    coxv = popc(Xp[v] & Xp[x]) - 2 * inv
+                    tri3 = popc(Xp[v] & Xp[a] & Xp[x]) - 1 - 2 * inv
+                W1 += coxv - 1
+                W2 += tri3
+                W3 += tri3 if inv else 0
+        k = comb(c - 1, 3) - nv * comb(c - 2, 2) - (M - nv) * (c - 3)
+        k += (comb(nv, 2) + s1[v]) * (c - 3)
+        k += nv * (M - nv + 1) - sums["nb"] + P - comb(nv, 2) - s1[v]
+        k -= t * (c - 3) + (T - t) + comb(nv, 3) + sums["cnb"]
+        k -= sums["s1"] - nv * (nv - 1) + (nv - 1) * s1[v] - 4 * t
+        k += (W1 - nv * (nv - 1)) // 2                                   # 4-cycles
+        k += t * (nv - 2) + sums["nbco"] - 4 * t + sums["tt"] - sums["co"]  # paws
+        k -= sums["cco"] + W2 // 2 - t                                    # diamonds
+        k += W3 // 6                                                      # K4s
+        K[v] = k
+    return K
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_k4_word_level_model(seed):
+    rng = np.random.default_rng(300 + seed)
+    checked = 0
+    for _ in range(40):
+        n = int(rng.integers(6, 20))
+        p = rng.choice([0.85, 0.93, 1.0])
+        U = np.triu(rng.random((n, n)) < p, 1)
+        A = U | U.T
+        rows = [sum(1 << j for j in range(n) if A[i, j]) for i in range(n)]
+        sub = [v for v in range(n) if rng.random() < 0.75]
+        if len(sub) < 4:
+            continue
+        K = k4_word_level(rows, sum(1 << v for v in sub))
+        if K is None:
+            continue
+        b = k4_through_brute(A[np.ix_(sub, sub)].astype(np.int64))
+        assert [K[v] for v in sub] == b.tolist()
+        checked += 1
+    assert checked > 10
